@@ -1,0 +1,134 @@
+"""CPU oracle for the proper-order multi-column min-cut — TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg
+of ``bench.py`` may import this package. The product path (the CUDA library and its
+binding) never does, and this package imports nothing from it.
+
+``solve`` builds the literal explicit-edge s-t graph of Section 1.2 and runs Dinic's
+blocking-flow max-flow (Section 2) in plain C (``pog_oracle.c``), int64 throughout.
+Its result is the max-flow value (Eq. 5), the minimal minimum cut (nodes reachable
+from s in the final residual graph; the cut of Theorem 1.1) and the surface height
+of each column, the top node of the cut in that column.
+
+Pins (see ``tests/test_oracle_pins.py``): brute-force enumeration of all feasible
+surfaces on tiny volumes, the closed form for delta >= Z-1 without soft penalty,
+an exact dynamic program over one row of columns, the energy/flow identity, and the
+capacity / conservation / max-flow = min-cut invariants checked inside the C code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pog_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {0: "ok", 1: "bad arguments", 2: "out of memory", 3: "capacity violated",
+          4: "conservation violated", 5: "flow != cut capacity", 6: "empty column in cut"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-Wextra",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _configure(lib):
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_solve.restype = ctypes.c_int
+    lib.oracle_solve.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, i64p, i32p, i64p]
+    lib.oracle_energy.restype = ctypes.c_int64
+    lib.oracle_energy.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_int64, i32p, i32p]
+    lib.oracle_cut_capacity.restype = ctypes.c_int64
+    lib.oracle_cut_capacity.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int64, i32p]
+    return lib
+
+
+def load_library(path: str):
+    """Load an oracle build from an explicit path (used to test planted mistakes)."""
+    return _configure(ctypes.CDLL(path))
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _configure(ctypes.CDLL(build()))
+    return _lib
+
+
+def _i32(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _cost(cost) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(cost), dtype=np.int32)
+    if c.ndim != 3:
+        raise ValueError("cost must be [X, Y, Z]")
+    return c
+
+
+class OracleResult:
+    def __init__(self, flow, heights, phases, augmentations, nodes, half_arcs):
+        self.flow = flow
+        self.heights = heights
+        self.phases = phases
+        self.augmentations = augmentations
+        self.nodes = nodes
+        self.half_arcs = half_arcs
+
+    def __repr__(self):
+        return (f"OracleResult(flow={self.flow}, phases={self.phases}, "
+                f"augmentations={self.augmentations}, nodes={self.nodes})")
+
+
+def solve(cost, delta: int, alpha: int, check: bool = False, lib=None) -> OracleResult:
+    """Max-flow value and minimal-cut surface of one int32 [X, Y, Z] cost volume."""
+    lib = lib or _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    heights = np.empty((X, Y), dtype=np.int32)
+    flow = ctypes.c_int64(0)
+    stats = (ctypes.c_int64 * 4)()
+    rc = lib.oracle_solve(_i32(c), X, Y, Z, int(delta), int(alpha), 1 if check else 0,
+                          ctypes.byref(flow), _i32(heights), stats)
+    if rc != 0:
+        raise RuntimeError(f"oracle_solve failed: {ERRORS.get(rc, rc)}")
+    return OracleResult(int(flow.value), heights, *[int(v) for v in stats])
+
+
+def energy(cost, heights, delta: int, alpha: int):
+    """(E, feasible): Eq. 1 with E_feature = sum_col c(col, h) and E_prior =
+    alpha * sum over unordered 4-neighbour pairs |h_p - h_q|."""
+    lib = _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
+    feas = ctypes.c_int32(0)
+    e = lib.oracle_energy(_i32(c), X, Y, Z, int(delta), int(alpha), _i32(h), ctypes.byref(feas))
+    return int(e), bool(feas.value)
+
+
+def cut_capacity(cost, heights, delta: int, alpha: int) -> int:
+    """Eq. 6 for the cut below the surface (z <= h in every column), arc by arc over the
+    literal graph; -1 when an infinite arc crosses it."""
+    lib = _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
+    return int(lib.oracle_cut_capacity(_i32(c), X, Y, Z, int(delta), int(alpha), _i32(h)))

@@ -1,0 +1,383 @@
+/*
+ * CPU oracle for the proper-order multi-column min-cut. TEST INFRASTRUCTURE ONLY:
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark may call
+ * it. It shares no code with the CUDA path.
+ *
+ * What it computes (plain and slow on purpose):
+ *   1. The literal s-t graph of the optimal net-surface problem (Section 1.2): every
+ *      node weight w(v) becomes a terminal arc, every proper-order edge becomes an
+ *      explicit arc with an explicit reverse half-arc. Nothing is contracted or
+ *      dropped; the edge list is stored, the opposite of the implicit addressing of
+ *      Section 3.2.3.
+ *   2. Dinic's blocking-flow max-flow (Section 2), int64 capacities.
+ *   3. The minimal minimum cut: the nodes reachable from s in the final residual
+ *      graph, and from it the surface height of each column.
+ *   4. The surface energy of Eq. 1 and the cut capacity of Eq. 6, from their
+ *      definitions, for the identities that pin the oracle.
+ *
+ * Graph (z fastest: node (x,y,z) has index (x*Y + y)*Z + z; s = N, t = N+1):
+ *   w(x,y,z) = c(x,y,z) - c(x,y,z-1) for z > 0, w(x,y,0) = c(x,y,0), and
+ *   w(0,0,0) is further lowered by 1 + sum_{x,y} c(x,y,0) so the cut is never empty.
+ *   s -> v with capacity -w(v) when w(v) < 0; v -> t with capacity w(v) when w(v) > 0.
+ *   (x,y,z) -> (x,y,z-1), infinite, for z >= 1            (column order)
+ *   (x,y,z) -> (x',y',max(0,z-delta)), infinite            (hard smoothness, each
+ *                                                           in-grid 4-neighbour)
+ *   (x,y,z) -> (x',y',z), capacity alpha, if alpha > 0     (soft smoothness: one arc
+ *                                                           per ordered neighbour pair)
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_INF ((int64_t)1 << 62)
+
+enum { ORC_OK = 0, ORC_E_ARGS = 1, ORC_E_NOMEM = 2, ORC_E_CAPACITY = 3,
+       ORC_E_CONSERVATION = 4, ORC_E_CUT = 5, ORC_E_SURFACE = 6 };
+
+typedef struct {
+    int64_t n;        /* nodes including s and t */
+    int64_t m;        /* half-arcs */
+    int64_t *first;   /* CSR row starts, n+1 entries */
+    int32_t *head;    /* head node of each half-arc */
+    int64_t *rev;     /* index of the paired half-arc */
+    int64_t *cap;     /* residual capacity */
+    int64_t *cap0;    /* initial capacity (only when invariants are checked) */
+    int64_t *fill;    /* scratch: next free slot per node during construction */
+} orc_graph;
+
+static int64_t idx3(int32_t Y, int32_t Z, int64_t x, int64_t y, int64_t z) {
+    return (x * Y + y) * Z + z;
+}
+
+/* Node weight of Section 1.2 (the bottom node of column (0,0) carries the offset). */
+static int64_t node_weight(const int32_t *c, int32_t X, int32_t Y, int32_t Z,
+                           int64_t x, int64_t y, int64_t z, int64_t bottom_sum) {
+    (void)X;
+    int64_t w = (z > 0) ? (int64_t)c[idx3(Y, Z, x, y, z)] - (int64_t)c[idx3(Y, Z, x, y, z - 1)]
+                        : (int64_t)c[idx3(Y, Z, x, y, 0)];
+    if (x == 0 && y == 0 && z == 0) w -= 1 + bottom_sum;
+    return w;
+}
+
+static int64_t bottom_layer_sum(const int32_t *c, int32_t X, int32_t Y, int32_t Z) {
+    int64_t s = 0;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y) s += c[idx3(Y, Z, x, y, 0)];
+    return s;
+}
+
+static const int DX[4] = {-1, 1, 0, 0};
+static const int DY[4] = {0, 0, -1, 1};
+
+/* Visit every arc of the literal graph once. mode 0 counts half-arcs per node,
+ * mode 1 places them. */
+static void add_arc(orc_graph *g, int mode, int64_t u, int64_t v, int64_t c) {
+    if (mode == 0) {
+        g->first[u + 1]++;
+        g->first[v + 1]++;
+        return;
+    }
+    int64_t a = g->fill[u]++;
+    int64_t b = g->fill[v]++;
+    g->head[a] = (int32_t)v;
+    g->head[b] = (int32_t)u;
+    g->rev[a] = b;
+    g->rev[b] = a;
+    g->cap[a] = c;
+    g->cap[b] = 0;
+    if (g->cap0) {
+        g->cap0[a] = c;
+        g->cap0[b] = 0;
+    }
+}
+
+static void enumerate_arcs(orc_graph *g, int mode, const int32_t *c, int32_t X, int32_t Y,
+                           int32_t Z, int32_t delta, int64_t alpha) {
+    const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
+    const int64_t bsum = bottom_layer_sum(c, X, Y, Z);
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t z = 0; z < Z; ++z) {
+                const int64_t v = idx3(Y, Z, x, y, z);
+                const int64_t w = node_weight(c, X, Y, Z, x, y, z, bsum);
+                if (w < 0) add_arc(g, mode, s, v, -w);
+                if (w > 0) add_arc(g, mode, v, t, w);
+                if (z >= 1) add_arc(g, mode, v, idx3(Y, Z, x, y, z - 1), ORC_INF);
+                for (int d = 0; d < 4; ++d) {
+                    const int64_t xq = x + DX[d], yq = y + DY[d];
+                    if (xq < 0 || xq >= X || yq < 0 || yq >= Y) continue;
+                    const int64_t zq = (z - delta > 0) ? z - delta : 0;
+                    add_arc(g, mode, v, idx3(Y, Z, xq, yq, zq), ORC_INF);
+                    if (alpha > 0) add_arc(g, mode, v, idx3(Y, Z, xq, yq, z), alpha);
+                }
+            }
+}
+
+static void graph_free(orc_graph *g) {
+    free(g->first);
+    free(g->head);
+    free(g->rev);
+    free(g->cap);
+    free(g->cap0);
+    free(g->fill);
+    memset(g, 0, sizeof *g);
+}
+
+static int graph_build(orc_graph *g, const int32_t *c, int32_t X, int32_t Y, int32_t Z,
+                       int32_t delta, int64_t alpha, int keep_cap0) {
+    memset(g, 0, sizeof *g);
+    const int64_t N = (int64_t)X * Y * Z;
+    g->n = N + 2;
+    g->first = calloc((size_t)g->n + 1, sizeof(int64_t));
+    if (!g->first) return ORC_E_NOMEM;
+    enumerate_arcs(g, 0, c, X, Y, Z, delta, alpha);
+    for (int64_t i = 0; i < g->n; ++i) g->first[i + 1] += g->first[i];
+    g->m = g->first[g->n];
+    g->head = malloc((size_t)g->m * sizeof(int32_t));
+    g->rev = malloc((size_t)g->m * sizeof(int64_t));
+    g->cap = malloc((size_t)g->m * sizeof(int64_t));
+    g->fill = malloc((size_t)g->n * sizeof(int64_t));
+    if (keep_cap0) g->cap0 = malloc((size_t)g->m * sizeof(int64_t));
+    if (!g->head || !g->rev || !g->cap || !g->fill || (keep_cap0 && !g->cap0)) {
+        graph_free(g);
+        return ORC_E_NOMEM;
+    }
+    memcpy(g->fill, g->first, (size_t)g->n * sizeof(int64_t));
+    enumerate_arcs(g, 1, c, X, Y, Z, delta, alpha);
+    free(g->fill);
+    g->fill = NULL;
+    return ORC_OK;
+}
+
+/* Dinic (Section 2): BFS levels from s over residual arcs, then a blocking flow of
+ * shortest augmenting paths found by depth-first search with a current-arc pointer
+ * per node; repeat until t is unreachable. */
+typedef struct {
+    int32_t *level;
+    int64_t *queue;
+    int64_t *iter;
+    int64_t *path;
+    int64_t phases;
+    int64_t augmentations;
+} orc_dinic;
+
+static int dinic_bfs(const orc_graph *g, orc_dinic *d, int64_t s, int64_t t) {
+    for (int64_t i = 0; i < g->n; ++i) d->level[i] = -1;
+    int64_t qh = 0, qt = 0;
+    d->level[s] = 0;
+    d->queue[qt++] = s;
+    while (qh < qt) {
+        const int64_t u = d->queue[qh++];
+        for (int64_t a = g->first[u]; a < g->first[u + 1]; ++a) {
+            const int64_t v = g->head[a];
+            if (g->cap[a] > 0 && d->level[v] < 0) {
+                d->level[v] = d->level[u] + 1;
+                d->queue[qt++] = v;
+            }
+        }
+    }
+    return d->level[t] >= 0;
+}
+
+static int64_t dinic_blocking_flow(orc_graph *g, orc_dinic *d, int64_t s, int64_t t) {
+    int64_t total = 0, depth = 0, u = s;
+    memcpy(d->iter, g->first, (size_t)g->n * sizeof(int64_t));
+    for (;;) {
+        if (u == t) {
+            int64_t b = ORC_INF;
+            for (int64_t k = 0; k < depth; ++k)
+                if (g->cap[d->path[k]] < b) b = g->cap[d->path[k]];
+            int64_t cut_at = -1;
+            for (int64_t k = 0; k < depth; ++k) {
+                const int64_t a = d->path[k];
+                g->cap[a] -= b;
+                g->cap[g->rev[a]] += b;
+                if (cut_at < 0 && g->cap[a] == 0) cut_at = k;
+            }
+            total += b;
+            d->augmentations++;
+            /* resume from the tail of the first arc this augmentation saturated */
+            depth = cut_at;
+            u = (depth == 0) ? s : g->head[d->path[depth - 1]];
+            continue;
+        }
+        int64_t a = d->iter[u];
+        for (; a < g->first[u + 1]; ++a) {
+            const int64_t v = g->head[a];
+            if (g->cap[a] > 0 && d->level[v] == d->level[u] + 1) break;
+        }
+        d->iter[u] = a;
+        if (a < g->first[u + 1]) {
+            d->path[depth++] = a;
+            u = g->head[a];
+        } else {
+            d->level[u] = -1; /* dead end for this phase */
+            if (u == s) break;
+            const int64_t back = d->path[--depth];
+            u = g->head[g->rev[back]];
+            d->iter[u]++;
+        }
+    }
+    return total;
+}
+
+/* Nodes reachable from s over residual arcs: the source side of the minimal min cut. */
+static void residual_reach(const orc_graph *g, int64_t s, uint8_t *in_s, int64_t *queue) {
+    memset(in_s, 0, (size_t)g->n);
+    int64_t qh = 0, qt = 0;
+    in_s[s] = 1;
+    queue[qt++] = s;
+    while (qh < qt) {
+        const int64_t u = queue[qh++];
+        for (int64_t a = g->first[u]; a < g->first[u + 1]; ++a) {
+            const int64_t v = g->head[a];
+            if (g->cap[a] > 0 && !in_s[v]) {
+                in_s[v] = 1;
+                queue[qt++] = v;
+            }
+        }
+    }
+}
+
+/* Capacity (Eq. 2), antisymmetric bookkeeping (Eq. 3) and conservation (Eq. 4) of the
+ * final flow, and max-flow = min-cut (Theorem 1.1) on the cut found. */
+static int check_invariants(const orc_graph *g, int64_t s, int64_t t, const uint8_t *in_s,
+                            int64_t flow) {
+    int64_t *net = calloc((size_t)g->n, sizeof(int64_t));
+    if (!net) return ORC_E_NOMEM;
+    int64_t cut = 0;
+    int rc = ORC_OK;
+    for (int64_t u = 0; u < g->n && rc == ORC_OK; ++u)
+        for (int64_t a = g->first[u]; a < g->first[u + 1]; ++a) {
+            const int64_t f = g->cap0[a] - g->cap[a]; /* flow on this half-arc */
+            if (g->cap[a] < 0 || f > g->cap0[a]) { rc = ORC_E_CAPACITY; break; }
+            if (f != -(g->cap0[g->rev[a]] - g->cap[g->rev[a]])) { rc = ORC_E_CAPACITY; break; }
+            net[u] -= f; /* f > 0 leaves u; f < 0 on a reverse half-arc enters u */
+            if (in_s[u] && !in_s[g->head[a]]) cut += g->cap0[a];
+        }
+    if (rc == ORC_OK) {
+        for (int64_t v = 0; v < g->n; ++v)
+            if (v != s && v != t && net[v] != 0) { rc = ORC_E_CONSERVATION; break; }
+        if (rc == ORC_OK && (net[t] != flow || net[s] != -flow)) rc = ORC_E_CONSERVATION;
+        if (rc == ORC_OK && cut != flow) rc = ORC_E_CUT;
+    }
+    free(net);
+    return rc;
+}
+
+/*
+ * Solve one volume. cost: int32 [X][Y][Z] (z fastest). heights_out: int32 [X*Y],
+ * column (x,y) at x*Y + y. stats_out (may be NULL): phases, augmentations, nodes,
+ * half-arcs. check != 0 keeps the initial capacities and verifies Eq. 2-4 and
+ * Theorem 1.1 on the result.
+ */
+int oracle_solve(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                 int64_t alpha, int32_t check, int64_t *flow_out, int32_t *heights_out,
+                 int64_t *stats_out) {
+    if (!cost || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 || !flow_out || !heights_out)
+        return ORC_E_ARGS;
+    if ((int64_t)X * Y * Z + 2 > INT32_MAX) return ORC_E_ARGS;
+    orc_graph g;
+    int rc = graph_build(&g, cost, X, Y, Z, delta, alpha, check != 0);
+    if (rc != ORC_OK) return rc;
+    const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
+    orc_dinic d = {0};
+    d.level = malloc((size_t)g.n * sizeof(int32_t));
+    d.queue = malloc((size_t)g.n * sizeof(int64_t));
+    d.iter = malloc((size_t)g.n * sizeof(int64_t));
+    d.path = malloc((size_t)g.n * sizeof(int64_t));
+    uint8_t *in_s = malloc((size_t)g.n);
+    if (!d.level || !d.queue || !d.iter || !d.path || !in_s) {
+        rc = ORC_E_NOMEM;
+        goto done;
+    }
+    int64_t flow = 0;
+    while (dinic_bfs(&g, &d, s, t)) {
+        d.phases++;
+        flow += dinic_blocking_flow(&g, &d, s, t);
+    }
+    residual_reach(&g, s, in_s, d.queue);
+    for (int64_t col = 0; col < (int64_t)X * Y; ++col) {
+        int32_t h = -1;
+        for (int64_t z = 0; z < Z; ++z)
+            if (in_s[col * Z + z]) h = (int32_t)z;
+        heights_out[col] = h;
+        if (h < 0) rc = ORC_E_SURFACE;
+    }
+    if (rc == ORC_OK && check) rc = check_invariants(&g, s, t, in_s, flow);
+    *flow_out = flow;
+    if (stats_out) {
+        stats_out[0] = d.phases;
+        stats_out[1] = d.augmentations;
+        stats_out[2] = g.n;
+        stats_out[3] = g.m;
+    }
+done:
+    free(d.level);
+    free(d.queue);
+    free(d.iter);
+    free(d.path);
+    free(in_s);
+    graph_free(&g);
+    return rc;
+}
+
+/*
+ * Surface energy of Eq. 1 for a height map: E = sum_col c(col, h(col)) +
+ * alpha * sum over unordered 4-neighbour pairs |h_p - h_q|. *feasible is set to 0 if
+ * some pair differs by more than delta or a height is outside [0, Z).
+ */
+int64_t oracle_energy(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                      int64_t alpha, const int32_t *h, int32_t *feasible) {
+    int64_t e = 0;
+    int ok = 1;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y) {
+            const int64_t hp = h[x * Y + y];
+            if (hp < 0 || hp >= Z) { ok = 0; continue; }
+            e += cost[idx3(Y, Z, x, y, hp)];
+            if (x + 1 < X) {
+                const int64_t dq = hp - h[(x + 1) * Y + y];
+                const int64_t ad = dq < 0 ? -dq : dq;
+                if (ad > delta) ok = 0;
+                e += alpha * ad;
+            }
+            if (y + 1 < Y) {
+                const int64_t dq = hp - h[x * Y + y + 1];
+                const int64_t ad = dq < 0 ? -dq : dq;
+                if (ad > delta) ok = 0;
+                e += alpha * ad;
+            }
+        }
+    if (feasible) *feasible = ok;
+    return e;
+}
+
+/*
+ * Capacity (Eq. 6) of the s-t cut whose source side is {s} and, in each column, the
+ * nodes z <= h(col), counted arc by arc over the literal graph. Returns -1 when an
+ * infinite arc crosses the cut (the surface violates the hard constraints).
+ */
+int64_t oracle_cut_capacity(const int32_t *cost, int32_t X, int32_t Y, int32_t Z,
+                            int32_t delta, int64_t alpha, const int32_t *h) {
+    const int64_t bsum = bottom_layer_sum(cost, X, Y, Z);
+    int64_t cut = 0;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t z = 0; z < Z; ++z) {
+                const int in_u = z <= h[x * Y + y];
+                const int64_t w = node_weight(cost, X, Y, Z, x, y, z, bsum);
+                if (w < 0 && !in_u) cut += -w;          /* s -> v with v outside */
+                if (w > 0 && in_u) cut += w;            /* v -> t with v inside  */
+                if (!in_u) continue;
+                if (z >= 1 && !(z - 1 <= h[x * Y + y])) return -1;
+                for (int d = 0; d < 4; ++d) {
+                    const int64_t xq = x + DX[d], yq = y + DY[d];
+                    if (xq < 0 || xq >= X || yq < 0 || yq >= Y) continue;
+                    const int64_t zq = (z - delta > 0) ? z - delta : 0;
+                    if (!(zq <= h[xq * Y + yq])) return -1;
+                    if (alpha > 0 && !(z <= h[xq * Y + yq])) cut += alpha;
+                }
+            }
+    return cut;
+}
