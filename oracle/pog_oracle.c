@@ -175,6 +175,9 @@ static int dinic_bfs(const orc_graph *g, orc_dinic *d, int64_t s, int64_t t) {
                 d->queue[qt++] = v;
             }
         }
+        /* Every node closer to s than t is labelled once t is; nodes left unlabelled
+         * lie at t's distance or beyond and can be on no shortest s-t path. */
+        if (d->level[t] >= 0) break;
     }
     return d->level[t] >= 0;
 }
