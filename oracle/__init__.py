@@ -33,6 +33,10 @@ _lib = None
 ERRORS = {0: "ok", 1: "bad arguments", 2: "out of memory", 3: "capacity violated",
           4: "conservation violated", 5: "flow != cut capacity", 6: "empty column in cut"}
 
+CERTIFY_ERRORS = {0: "ok", 2: "out of memory", 10: "arc capacity violated", 11: "excess != inflow - outflow",
+                  12: "preflow value != reported flow", 13: "cut != residual reach of the excess nodes",
+                  14: "heights != top of the cut", 15: "cut capacity of the surface != flow"}
+
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, no target-specific flags)."""
@@ -56,6 +60,9 @@ def _configure(lib):
     lib.oracle_cut_capacity.restype = ctypes.c_int64
     lib.oracle_cut_capacity.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int64, i32p]
+    lib.oracle_certify.restype = ctypes.c_int
+    lib.oracle_certify.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int64] + [i32p] * 7 + [ctypes.c_int64]
     return lib
 
 
@@ -132,3 +139,19 @@ def cut_capacity(cost, heights, delta: int, alpha: int) -> int:
     X, Y, Z = c.shape
     h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
     return int(lib.oracle_cut_capacity(_i32(c), X, Y, Z, int(delta), int(alpha), _i32(h)))
+
+
+def certify(cost, delta: int, alpha: int, state: dict, flow: int, heights) -> int:
+    """Check a solver's exported final state (the dict of ``pog_export_state``: excess,
+    sink, fdown, fhard, gsoft, in_cut) against (flow, heights) in O(N); 0 means the
+    preflow is feasible, its value is `flow`, the cut below `heights` has capacity
+    `flow`, and the cut is the residual reach of the excess nodes. See CERTIFY_ERRORS."""
+    lib = _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    arr = {k: np.ascontiguousarray(state[k], dtype=np.int32) for k in
+           ("excess", "sink", "fdown", "fhard", "gsoft", "in_cut")}
+    h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
+    return int(lib.oracle_certify(_i32(c), X, Y, Z, int(delta), int(alpha), _i32(arr["excess"]),
+                                  _i32(arr["sink"]), _i32(arr["fdown"]), _i32(arr["fhard"]),
+                                  _i32(arr["gsoft"]), _i32(arr["in_cut"]), _i32(h), int(flow)))

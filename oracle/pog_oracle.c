@@ -384,3 +384,132 @@ int64_t oracle_cut_capacity(const int32_t *cost, int32_t X, int32_t Y, int32_t Z
             }
     return cut;
 }
+
+/*
+ * Optimality certificate of a solver's final residual state, for volumes too large for
+ * Dinic. The state is the one include/pog.h exports (int32 arrays of N = X*Y*Z nodes,
+ * z fastest): excess, sink residual, flow on the down arc, flow on the hard arc of each
+ * direction d (fhard[d*N + v]), net soft flow towards x+1 / y+1 (gsoft[k*N + v]), the
+ * cut marks, and the heights. In that state the bottom layer z = 0 is merged into the
+ * source: it is in every minimum cut (its weights sum to -1 and every non-empty closed
+ * set contains it), so arcs into it carry no flow and its sink arcs add
+ * sum_{z=0, w>0} w to the flow value.
+ *
+ * Checks, in order (return code):
+ *   capacity (Eq. 2) of every arc and sink arc, zero flow on absent arcs      -> 10
+ *   excess = inflow - outflow (Eq. 4 relaxed to a preflow) and excess >= 0     -> 11
+ *   flow value (Eq. 5) of the preflow equals `flow`                          -> 12
+ *   the cut marks equal the residual reach of the nodes with excess           -> 13
+ *   each height is the top marked node of its column (0 if none)              -> 14
+ *   the capacity (Eq. 6) of the cut below the heights equals `flow`           -> 15
+ * The last check with a feasible preflow of value `flow` proves both optimal
+ * (Theorem 1.1); the reach check proves the cut is the minimal one.
+ */
+int oracle_certify(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta, int64_t alpha,
+                   const int32_t *excess, const int32_t *sink, const int32_t *fdown, const int32_t *fhard,
+                   const int32_t *gsoft, const int32_t *in_cut, const int32_t *heights, int64_t flow) {
+    const int64_t N = (int64_t)X * Y * Z;
+    const int64_t bsum = bottom_layer_sum(cost, X, Y, Z);
+    int64_t *net = calloc((size_t)N, sizeof(int64_t));
+    uint8_t *seen = calloc((size_t)N, 1);
+    int64_t *queue = malloc((size_t)N * sizeof(int64_t));
+    int rc = ORC_OK;
+    if (!net || !seen || !queue) {
+        rc = ORC_E_NOMEM;
+        goto out;
+    }
+    int64_t value = 0;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t z = 0; z < Z; ++z) {
+                const int64_t v = idx3(Y, Z, x, y, z);
+                const int64_t w = node_weight(cost, X, Y, Z, x, y, z, bsum);
+                if (z == 0) { /* part of the source: no state of its own */
+                    if (w > 0) value += w;
+                    if (sink[v] != 0 || fdown[v] != 0 || excess[v] != 0) { rc = 10; goto out; }
+                    for (int d = 0; d < 4; ++d)
+                        if (fhard[d * N + v] != 0 || (alpha > 0 && gsoft && d < 2 && gsoft[d * N + v] != 0)) {
+                            rc = 10;
+                            goto out;
+                        }
+                    continue;
+                }
+                const int64_t snk0 = w > 0 ? w : 0;
+                if (sink[v] < 0 || sink[v] > snk0) { rc = 10; goto out; }
+                net[v] += (w < 0 ? -w : 0) - (snk0 - sink[v]);
+                value += snk0 - sink[v];
+                if (z >= 2) {
+                    if (fdown[v] < 0) { rc = 10; goto out; }
+                    net[v] -= fdown[v];
+                    net[v - 1] += fdown[v];
+                } else if (fdown[v] != 0) { rc = 10; goto out; }
+                for (int d = 0; d < 4; ++d) {
+                    const int64_t xq = x + DX[d], yq = y + DY[d];
+                    const int64_t f = fhard[d * N + v];
+                    const int in_grid = xq >= 0 && xq < X && yq >= 0 && yq < Y;
+                    if (in_grid && z - delta >= 1) {
+                        if (f < 0) { rc = 10; goto out; }
+                        const int64_t head = idx3(Y, Z, xq, yq, z - delta);
+                        net[v] -= f;
+                        net[head] += f;
+                    } else if (f != 0) { rc = 10; goto out; }
+                    if (alpha > 0 && gsoft && (d & 1)) { /* the pair towards x+1 / y+1 */
+                        const int64_t g = gsoft[(d >> 1) * N + v];
+                        if (in_grid) {
+                            if (g < -alpha || g > alpha) { rc = 10; goto out; }
+                            net[v] -= g;
+                            net[idx3(Y, Z, xq, yq, z)] += g;
+                        } else if (g != 0) { rc = 10; goto out; }
+                    }
+                }
+            }
+    for (int64_t v = 0; v < N; ++v) {
+        if (v % Z == 0) continue;
+        if (net[v] != excess[v] || excess[v] < 0) { rc = 11; goto out; }
+    }
+    if (value != flow) { rc = 12; goto out; }
+    /* residual reach of the excess nodes (z >= 1 only; the bottom layer is the source) */
+    int64_t qh = 0, qt = 0;
+    for (int64_t v = 0; v < N; ++v)
+        if (v % Z != 0 && excess[v] > 0) { seen[v] = 1; queue[qt++] = v; }
+    while (qh < qt) {
+        const int64_t u = queue[qh++];
+        const int64_t z = u % Z, col = u / Z, x = col / Y, y = col % Y;
+        int64_t nbr[16];
+        int k = 0;
+        if (z >= 2) nbr[k++] = u - 1;                      /* down arc: infinite */
+        if (z + 1 < Z && fdown[u + 1] > 0) nbr[k++] = u + 1; /* reverse of the up node's down arc */
+        for (int d = 0; d < 4; ++d) {
+            const int64_t xq = x + DX[d], yq = y + DY[d];
+            if (xq < 0 || xq >= X || yq < 0 || yq >= Y) continue;
+            if (z - delta >= 1) nbr[k++] = idx3(Y, Z, xq, yq, z - delta); /* hard arc: infinite */
+            if (z + delta < Z) {                                        /* reverse of a hard arc into u */
+                const int64_t w = idx3(Y, Z, xq, yq, z + delta);
+                if (fhard[(d ^ 1) * N + w] > 0) nbr[k++] = w;
+            }
+            if (alpha > 0 && gsoft) {
+                const int64_t q = idx3(Y, Z, xq, yq, z);
+                const int64_t g = (d & 1) ? gsoft[(d >> 1) * N + u] : -gsoft[(d >> 1) * N + q];
+                if (alpha - g > 0) nbr[k++] = q; /* g: net flow u -> q */
+            }
+        }
+        for (int i = 0; i < k; ++i)
+            if (!seen[nbr[i]]) { seen[nbr[i]] = 1; queue[qt++] = nbr[i]; }
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        if (v % Z == 0) continue;
+        if ((in_cut[v] != 0) != (seen[v] != 0)) { rc = 13; goto out; }
+    }
+    for (int64_t col = 0; col < (int64_t)X * Y; ++col) {
+        int32_t top = 0;
+        for (int64_t z = 1; z < Z; ++z)
+            if (in_cut[col * Z + z]) top = (int32_t)z;
+        if (heights[col] != top) { rc = 14; goto out; }
+    }
+    if (oracle_cut_capacity(cost, X, Y, Z, delta, alpha, heights) != flow) rc = 15;
+out:
+    free(net);
+    free(seen);
+    free(queue);
+    return rc;
+}

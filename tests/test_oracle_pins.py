@@ -191,3 +191,87 @@ def test_planted_mistakes(name, tmp_path):
 
 def test_unmutated_passes_mutant_pins():
     assert _pins_pass(oracle._load())
+
+
+# --------------------------------------------------------------------------------------
+# The O(N) certificate used at sizes Dinic cannot reach, pinned on states whose status is
+# known: the empty preflow (feasible; optimal exactly when no node starts with excess).
+# --------------------------------------------------------------------------------------
+
+def _zero_state(cost, delta, alpha):
+    """The preflow before any push, in the exported layout, and its value."""
+    X, Y, Z = cost.shape
+    N = X * Y * Z
+    w = pins.node_weights(cost).reshape(-1)
+    upper = (np.arange(N) % Z) != 0
+    exc = np.where(upper & (w < 0), -w, 0).astype(np.int32)
+    snk = np.where(upper & (w > 0), w, 0).astype(np.int32)
+    st = dict(excess=exc, sink=snk, fdown=np.zeros(N, np.int32), fhard=np.zeros(4 * N, np.int32),
+              gsoft=np.zeros(2 * N, np.int32), in_cut=np.zeros(N, np.int32))
+    b = pins.node_weights(cost)[:, :, 0]
+    return st, int(b[b > 0].sum())
+
+
+def _reach_zero_state(cost, delta, alpha, st):
+    """Residual reach of the excess nodes in the untouched graph (python BFS, tiny only)."""
+    X, Y, Z = cost.shape
+    idx = lambda x, y, z: (x * Y + y) * Z + z  # noqa: E731
+    seen = set(int(v) for v in np.flatnonzero(st["excess"] > 0))
+    todo = list(seen)
+    while todo:
+        u = todo.pop()
+        z, col = u % Z, u // Z
+        x, y = col // Y, col % Y
+        nxt = [u - 1] if z >= 2 else []
+        for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+            xq, yq = x + dx, y + dy
+            if 0 <= xq < X and 0 <= yq < Y:
+                if z - delta >= 1:
+                    nxt.append(idx(xq, yq, z - delta))
+                if alpha > 0:
+                    nxt.append(idx(xq, yq, z))
+        for v in nxt:
+            if v not in seen:
+                seen.add(v)
+                todo.append(v)
+    cut = np.zeros(X * Y * Z, np.int32)
+    cut[list(seen)] = 1
+    return cut
+
+
+def test_certificate_accepts_optimal_empty_preflow():
+    rng = np.random.default_rng(31)
+    for _ in range(5):
+        cost = np.sort(rng.integers(-50, 50, size=(3, 4, 6)), axis=2).astype(np.int32)  # non-decreasing columns
+        st, value = _zero_state(cost, 2, 3)
+        heights = np.zeros((3, 4), np.int32)
+        assert oracle.solve(cost, 2, 3).flow == value
+        assert oracle.certify(cost, 2, 3, st, value, heights) == 0
+
+
+def test_certificate_rejects_broken_states():
+    rng = np.random.default_rng(32)
+    cost = rng.integers(-50, 50, size=(3, 4, 6)).astype(np.int32)
+    d, a = 1, 4
+    st, value = _zero_state(cost, d, a)
+    st["in_cut"] = _reach_zero_state(cost, d, a, st)
+    top = np.where(st["in_cut"].reshape(3, 4, 6).astype(bool), np.arange(6), 0).max(axis=2).astype(np.int32)
+    # feasible but not optimal: everything holds except the cut capacity
+    assert oracle.certify(cost, d, a, st, value, top) == 15
+    assert oracle.certify(cost, d, a, st, value + 1, top) == 12
+    bad = {k: v.copy() for k, v in st.items()}
+    bad["excess"][np.flatnonzero(bad["excess"])[0]] += 1
+    assert oracle.certify(cost, d, a, bad, value, top) == 11
+    bad = {k: v.copy() for k, v in st.items()}
+    bad["fdown"][0] = 1  # a bottom node has no down arc
+    assert oracle.certify(cost, d, a, bad, value, top) == 10
+    bad = {k: v.copy() for k, v in st.items()}
+    bad["gsoft"][7] = a + 1
+    assert oracle.certify(cost, d, a, bad, value, top) in (10, 11)
+    bad = {k: v.copy() for k, v in st.items()}
+    off = np.flatnonzero((bad["in_cut"] == 1) & (np.arange(72) % 6 != 0))[0]
+    bad["in_cut"][off] = 0
+    assert oracle.certify(cost, d, a, bad, value, top) == 13
+    wrong = top.copy()
+    wrong[0, 0] = (wrong[0, 0] + 1) % 6
+    assert oracle.certify(cost, d, a, st, value, wrong) == 14
