@@ -1,0 +1,308 @@
+"""Benchmark: min-cut solve throughput (Mnodes/s) on the 512x512x384 seismic-scale volume.
+
+One step = one whole solve of the volume through the C ABI: graph construction
+(pog_build), push-relabel with global relabels to a maximum preflow, cut extraction and
+surface heights (pog_maxflow + pog_surface). `value` times steps whose input already
+sits in HBM; `e2e` times the same solve from a pinned host buffer, with the H2D copy of
+the costs and the D2H read of the heights and flow inside the timed region.
+
+--impl reference times the CPU oracle (explicit-edge Dinic) on a bounded crop of the same
+workload. Several GPUs: one independent replica per rank (the single-volume solve does
+not shard), max-over-ranks timing, value = all ranks' nodes / that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "min-cut solve Mnodes/s at 512x512x384 (plain vs batched); % of HBM roofline"
+UNIT = "Mnodes/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(name):
+    from paper_2601_17026_gb300 import synth
+
+    if name == "seismic":
+        return synth.seismic_volume()
+    if name == "medium":
+        return synth.medium_volume()
+    if name == "small":
+        return synth.small_volume()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def algorithmic_bytes(N, alpha):
+    """Per-launch algorithmic bytes of each kernel family (see the roofline notes in DESIGN)."""
+    arc_words = 1 + 4 + (2 if alpha > 0 else 0)  # down flow, 4 hard flows, 2 soft pair values
+    S = 4 * (4 + arc_words)  # label, excess, sink residual + arc words
+    return {
+        "sweep": 2 * S * N,            # one push/relabel pass over the state: read + write
+        "bfs": (4 + 4 * arc_words) * N + 4 * N,  # labels + arc residuals read, labels written
+        "cut": (4 + 4 * arc_words) * N + 4 * N,
+        "build": 4 * N + S * N,        # costs read, state written
+    }, S
+
+
+def run_ours(args):
+    import torch
+
+    import __graft_entry__
+    from paper_2601_17026_gb300 import pog
+
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    __graft_entry__.build()
+    vol = _workload(args.workload)
+    X, Y, Z = vol.cost.shape
+    N = vol.n
+    host = torch.from_numpy(vol.cost).pin_memory()
+    dev = host.cuda()
+    stream = torch.cuda.current_stream()
+    opts = pog.make_options(flags=pog.POG_FLAG_TIMING)
+
+    def step(src_dev):
+        with pog.pog_build(src_dev, vol.delta, vol.alpha, opts) as g:
+            flow = pog.pog_maxflow(g)
+            h = pog.pog_surface(g)
+            st = pog.pog_stats(g)
+        return flow, h, st
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flow0, h0, _ = step(dev)
+    h0 = h0.cpu()
+
+    # --- device-resident timed region
+    barrier()
+    stats = []
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            flow, h, st = step(dev)
+            stats.append(st)
+        t1.record(stream)
+        barrier()
+    ms = t0.elapsed_time(t1)
+    assert flow == flow0 and torch.equal(h.cpu(), h0), "solves of the same volume disagree"
+
+    # --- end to end from pinned host memory, through the public API
+    hbuf = torch.empty((X, Y), dtype=torch.int32).pin_memory()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d = host.to("cuda", non_blocking=True)
+        with pog.pog_build(d, vol.delta, vol.alpha) as g:
+            pog.pog_maxflow(g)  # flow value: 8 bytes read back
+            hbuf.copy_(pog.pog_surface(g), non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    times = [ms, e2e_ms]
+    if ws > 1:
+        t = torch.tensor(times, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        times = t.tolist()
+    ms, e2e_ms = times
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+
+    per_step = ms / args.steps
+    value = ws * N * args.steps / (ms / 1e3) / 1e6
+    e2e_value = ws * N * args.steps / (e2e_ms / 1e3) / 1e6
+    # roofline of the dominant kernel family, timed live with events on the solve stream
+    bytes_per, S = algorithmic_bytes(N, vol.alpha)
+    fam = {"sweep": ("sweep_ms", "sweeps"), "bfs": ("bfs_ms", "bfs_passes"), "cut": ("cut_ms", "cut_passes"),
+           "build": ("build_ms", None)}
+    tot = {k: sum(s[v[0]] for s in stats) for k, v in fam.items()}
+    launches = {k: (sum(s[v[1]] for s in stats) if v[1] else len(stats)) for k, v in fam.items()}
+    dom = max(tot, key=tot.get)
+    avg_ms = tot[dom] / max(launches[dom], 1)
+    peak, peak_src = _peaks()
+    achieved = bytes_per[dom] / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    kernel_name = {"sweep": "k_push_relabel", "bfs": "k_bfs_relax", "cut": "k_cut_relax", "build": "k_build"}[dom]
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{X}x{Y}x{Z} layered-horizon volume, delta={vol.delta}, alpha={vol.alpha}",
+                   "nodes": N, "state_bytes": int(st0["state_bytes"]),
+                   "l2": "inputs larger than L2 (cost 4N B, state ~%d B/node)" % S,
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * X * Y + 8},
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_src, "bytes_per_launch": bytes_per[dom],
+                     "launches_per_step": launches[dom] / len(stats), "avg_launch_ms": round(avg_ms, 5)},
+        "kernel_ms_per_step": {k: round(v / len(stats), 3) for k, v in tot.items()},
+        "solver": {k: st0[k] for k in ("rounds", "sweeps", "bfs_passes", "cut_passes", "gaps", "active_initial")},
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": clocks.summary(),
+        "flow": flow,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, vol)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _crop(vol, X, Y):
+    from paper_2601_17026_gb300.synth import Volume
+
+    return Volume(np.ascontiguousarray(vol.cost[:X, :Y, :]), vol.delta, vol.alpha)
+
+
+def cpu_baseline(args, vol, sample_xy=32):
+    """The oracle (explicit-edge Dinic, one core) on a bounded crop of the workload."""
+    import oracle
+
+    crop = _crop(vol, sample_xy, sample_xy)
+    t = time.perf_counter()
+    oracle.solve(crop.cost, crop.delta, crop.alpha)
+    dt = time.perf_counter() - t
+    return {"value": round(crop.n / dt / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample_xy}x{sample_xy}x{vol.cost.shape[2]} crop (x,y < {sample_xy}) of the workload, "
+                      f"{crop.n} nodes, {dt:.1f} s single-threaded explicit-edge Dinic"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import oracle
+
+    vol = _workload(args.workload)
+    crop = _crop(vol, 32, 32)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.solve(crop.cost[:8, :8], crop.delta, crop.alpha)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(crop.cost, crop.delta, crop.alpha)
+    dt = time.perf_counter() - t
+    value = crop.n * args.steps / dt / 1e6
+    X, Y, Z = vol.cost.shape
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{X}x{Y}x{Z} layered-horizon volume, delta={vol.delta}, alpha={vol.alpha}",
+                   "sample": "32x32 crop per step"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"32x32x{Z} crop of the workload ({crop.n} nodes) per step"},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="seismic", choices=["seismic", "medium", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * pog.h — C ABI of the GB300 min-cut solver for proper-order multi-column graphs.
+ *
+ * The problem (Section 1.2 and Section 1.3 of Chandramouli, "Parallel Algorithm For
+ * Finding The Minimum s-t Cut in a Structured 3-Dimensional Proper Order Graph"):
+ * a cost volume c(x, y, z) over X*Y columns of Z nodes defines the surface energy of
+ * Eq. 1,
+ *     E(h) = sum_col c(col, h(col)) + alpha * sum_{4-neighbour pairs} |h_p - h_q|,
+ * subject to |h_p - h_q| <= delta. Its minimiser is the source side of the minimum
+ * s-t cut (Theorem 1.1) of the proper-order graph whose node weights
+ * w(z) = c(z) - c(z-1) become terminal arcs. The library computes the maximum flow
+ * value (Eq. 5) and the surface of the minimal minimum cut (the nodes reachable from
+ * s in the final residual graph), whose height in each column is the top node of the
+ * cut there. Vertices and arcs are addressed implicitly from (x, y, z) (Section 3.2.3);
+ * no edge list exists anywhere.
+ *
+ * Layout: every volume is int32 (or float32) [X][Y][Z], z fastest: element (x, y, z)
+ * at ((x*Y + y)*Z + z) — a contiguous torch tensor of shape [X, Y, Z]. A height map is
+ * int32 [X][Y], column (x, y) at x*Y + y.
+ *
+ * Pointers: "device" pointers are CUDA global-memory addresses on the current device;
+ * "host" pointers are ordinary CPU memory. The caller owns every pointer it passes;
+ * the library never keeps one past the call (pog_build copies what it needs into its
+ * own state before its stream work completes) and never frees one.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ * stream). All device work of a graph is ordered on the stream given to pog_build.
+ *
+ * Errors: every call returns a pog_status. No call throws, traps, or aborts; device
+ * failures are reported through a device error word read back by the host. After an
+ * error other than POG_E_INVALID the graph may only be freed.
+ */
+#ifndef POG_H
+#define POG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define POG_API __attribute__((visibility("default")))
+#else
+#define POG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    POG_OK = 0,
+    POG_E_INVALID = 1,    /* bad argument: sizes < 1, delta/alpha < 0, NULL pointer, N too large */
+    POG_E_OVERFLOW = 2,   /* a cost with |c| >= 2^30, or an arc flow that reached the int32 range */
+    POG_E_NOMEM = 3,      /* device or pinned-host allocation failed */
+    POG_E_CUDA = 4,       /* a CUDA runtime call failed (launch, copy, sync) */
+    POG_E_NOCONVERGE = 5, /* the iteration cap of pog_options was reached */
+    POG_E_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    POG_E_STATE = 7       /* call out of order, e.g. pog_surface before pog_maxflow */
+} pog_status;
+
+/* Tuning knobs. Zero in a field selects the built-in default. */
+typedef struct {
+    int32_t sweeps_per_relabel; /* push/relabel sweeps between global relabels (Section 2.1) */
+    int32_t max_rounds;         /* cap on global-relabel rounds before POG_E_NOCONVERGE */
+    int32_t tile_sweeps;        /* local sweeps a thread block runs on its shared-memory tile */
+    int32_t flags;              /* POG_FLAG_* bits */
+    int32_t reserved[4];
+} pog_options;
+
+#define POG_FLAG_NO_GAP 1 /* disable the gap heuristic between global relabels */
+#define POG_FLAG_TIMING 2 /* time each kernel family with CUDA events on the graph's stream */
+
+/* Counters of the last pog_maxflow. */
+typedef struct {
+    int64_t rounds;          /* global relabels run (the initial one included) */
+    int64_t sweeps;          /* push/relabel sweep launches */
+    int64_t bfs_passes;      /* global-relabel relaxation passes */
+    int64_t cut_passes;      /* cut-extraction reachability passes */
+    int64_t gaps;            /* gap relabels that raised at least one label */
+    int64_t active_initial;  /* active nodes after the initial global relabel */
+    int64_t nodes;           /* X*Y*Z */
+    int64_t state_bytes;     /* device bytes of the residual state */
+    int64_t launches;        /* kernels launched by pog_build + pog_maxflow */
+    /* device milliseconds per kernel family, with POG_FLAG_TIMING only (else 0) */
+    double sweep_ms;         /* push/relabel sweeps */
+    double bfs_ms;           /* global-relabel relaxation passes */
+    double cut_ms;           /* cut-extraction passes */
+    double build_ms;         /* graph construction (pog_build) */
+} pog_stats_t;
+
+typedef struct pog_graph pog_graph; /* opaque; owns its device state */
+
+/*
+ * Build the residual graph of one volume (graph construction, Section 1.2; implicit
+ * addressing, Section 3.2.3) and initialise the preflow: node weights become source
+ * excess (w < 0) or sink residual (w > 0), all arc flows start at zero.
+ *   cost_dev : device, int32 [X][Y][Z], |c| < 2^30 (else POG_E_OVERFLOW from pog_maxflow).
+ *   X, Y, Z  : >= 1, X*Y*Z < 2^31.
+ *   delta    : hard smoothness, >= 0 (|h_p - h_q| <= delta).
+ *   alpha    : soft smoothness per unit height difference, 0 <= alpha < 2^30.
+ *   opt      : host, may be NULL (defaults).
+ *   stream   : cudaStream_t for all device work of this graph.
+ *   out      : host, receives the new graph; unchanged on error.
+ * Allocates device state of about 40 bytes per node (32 when alpha == 0). Work is
+ * enqueued on `stream`; `cost_dev` must stay valid until that work has run.
+ */
+POG_API pog_status pog_build(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                     int32_t alpha, const pog_options *opt, void *stream, pog_graph **out);
+
+/*
+ * As pog_build, from a float32 device volume quantised on the fly to
+ * cq = round_half_even(scale * c) (scale a power of two keeps the product exact).
+ * A value with |scale * c| >= 2^30 or not finite makes pog_maxflow return POG_E_OVERFLOW.
+ */
+POG_API pog_status pog_build_f32(const float *cost_dev, float scale, int32_t X, int32_t Y, int32_t Z,
+                         int32_t delta, int32_t alpha, const pog_options *opt, void *stream,
+                         pog_graph **out);
+
+/*
+ * As pog_build_f32, with `margin` added to the quantised cost of the node (x, y, h(x,y))
+ * of every column, where h_aug_dev is a device int32 [X][Y] surface. This builds the
+ * loss-augmented problem min_h [E(h) - margin * Hamming(h, h_aug)] (up to the constant
+ * margin * X * Y) of a structured hinge loss. 0 <= margin < 2^28.
+ */
+POG_API pog_status pog_build_f32_augmented(const float *cost_dev, float scale, const int32_t *h_aug_dev,
+                                           int32_t margin, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                                           int32_t alpha, const pog_options *opt, void *stream,
+                                           pog_graph **out);
+
+/*
+ * Run push-relabel (Section 2.1; Algorithm 2) with periodic global relabelling by a
+ * level-synchronous reverse BFS from the sink (Section 3.2.2; Algorithm 3), the gap
+ * heuristic, and an exact termination test (Section 3.2.4) to a maximum preflow; then
+ * extract the minimal minimum cut and the surface heights.
+ *   flow_out : host, receives the max-flow value (int64) of the literal s-t graph.
+ * Blocks the calling thread until the graph's stream has finished this work.
+ */
+POG_API pog_status pog_maxflow(pog_graph *g, int64_t *flow_out);
+
+/*
+ * Copy the surface heights of the last pog_maxflow.
+ *   heights_dev : device, int32 [X][Y], receives h(x, y) in [0, Z).
+ * Enqueued on the graph's stream (asynchronous). POG_E_STATE before pog_maxflow.
+ */
+POG_API pog_status pog_surface(pog_graph *g, int32_t *heights_dev);
+
+/*
+ * Optimal energy E*(h) of Eq. 1 (in the units of the built costs) of the last
+ * pog_maxflow, from the flow value: max-flow = E*(h) + K, where
+ * K = -1 - sum_col c(col, 0) + sum over nodes with w < 0 of -w (the cut capacity of
+ * Eq. 6 for the closed set below h, after the weights telescope along each column).
+ *   energy_out : host int64.
+ */
+POG_API pog_status pog_energy(const pog_graph *g, int64_t *energy_out);
+
+/*
+ * Energy of Eq. 1 of given surfaces on quantised float costs, one volume per entry:
+ *   energy[b] = sum_col round_half_even(scale * c[b][col][h]) + alpha * sum_pairs |h_p - h_q|.
+ * Device pointers: cost float32 [B][X][Y][Z], h int32 [B][X][Y], energy int64 [B].
+ * A height outside [0, Z) makes that volume's entry INT64_MIN. Enqueued on `stream`.
+ */
+POG_API pog_status pog_surface_energy(const float *cost_dev, float scale, const int32_t *h_dev, int32_t B,
+                                      int32_t X, int32_t Y, int32_t Z, int32_t alpha, int64_t *energy_dev,
+                                      void *stream);
+
+/* Counters of the last pog_maxflow. out: host. */
+POG_API pog_status pog_stats(const pog_graph *g, pog_stats_t *out);
+
+/*
+ * Download the residual state after pog_maxflow, for host-side certificates.
+ * Each pointer is host memory of N = X*Y*Z int32 (fh: 4*N, gs: 2*N when alpha > 0,
+ * else may be NULL); any may be NULL to skip it. Node (x,y,z) at ((x*Y+y)*Z+z).
+ *   excess : final excess of each node (z >= 1; z = 0 nodes report 0).
+ *   sink   : remaining residual capacity of the node's arc to the sink.
+ *   fdown  : flow on the infinite arc (x,y,z) -> (x,y,z-1), z >= 2.
+ *   fhard  : fhard[d*N + v]: flow on the infinite arc from v to its neighbour in
+ *            direction d (0: x-1, 1: x+1, 2: y-1, 3: y+1) at height z - delta
+ *            (present when z - delta >= 1).
+ *   gsoft  : gsoft[k*N + v]: net flow from v to its neighbour at x+1 (k = 0) or
+ *            y+1 (k = 1) at the same z, in [-alpha, alpha].
+ *   in_cut : 1 when the node is in the source side of the minimal minimum cut.
+ * Arcs into the bottom layer z = 0 carry no flow here: the bottom layer is always in
+ * the minimal cut, so the solver merges it into the source (its sink arcs add a
+ * constant to the flow value).
+ */
+POG_API pog_status pog_export_state(const pog_graph *g, int32_t *excess, int32_t *sink, int32_t *fdown,
+                            int32_t *fhard, int32_t *gsoft, int32_t *in_cut);
+
+/* Release the graph and its device state (synchronises its stream first). NULL is a no-op. */
+POG_API void pog_free(pog_graph *g);
+
+/* Static, human-readable text of a status. */
+POG_API const char *pog_strerror(pog_status s);
+
+/*
+ * Quantise a float32 device array to int32: out[i] = round_half_even(scale * in[i]).
+ * Same rule as pog_build_f32. Returns POG_E_OVERFLOW (after a stream sync) when some
+ * |scale * in[i]| >= 2^30 or is not finite.
+ */
+POG_API pog_status pog_quantise(const float *in_dev, int32_t *out_dev, int64_t n, float scale,
+                        void *stream);
+
+/*
+ * Backward of the optimal energy E*(c) = min_h E(h) with respect to the cost volume
+ * (Danskin's theorem: the one-hot of the optimal surface), combined with a second
+ * surface for the structured hinge loss:
+ *   grad[b][x][y][z] = g_energy[b] * [z == h[b][x][y]]
+ *                    + g_hinge[b]  * ([z == h_target[b][x][y]] - [z == h_hat[b][x][y]])
+ * Device pointers: grad float32 [B][X][Y][Z] (fully overwritten), h / h_target / h_hat
+ * int32 [B][X][Y] (h_target and h_hat may be NULL when g_hinge is NULL), g_energy and
+ * g_hinge float32 [B] (device; g_hinge may be NULL). Enqueued on `stream`.
+ */
+POG_API pog_status pog_backward(float *grad_dev, const int32_t *h_dev, const int32_t *h_target_dev,
+                        const int32_t *h_hat_dev, const float *g_energy_dev,
+                        const float *g_hinge_dev, int32_t B, int32_t X, int32_t Y, int32_t Z,
+                        void *stream);
+
+/* One volume of a batch: device cost pointer, sizes and smoothness. */
+typedef struct {
+    const int32_t *cost_dev;
+    int32_t X, Y, Z, delta, alpha;
+} pog_volume;
+
+/*
+ * Solve n independent volumes (sizes may differ). flows_out: host int64 [n];
+ * heights_dev[i]: device int32 [X_i][Y_i]. Blocks until done. The first failing
+ * volume's status is returned; flows of the others are still written.
+ */
+POG_API pog_status pog_solve_batch(int32_t n, const pog_volume *vols, const pog_options *opt,
+                           void *stream, int64_t *flows_out, int32_t *const *heights_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POG_H */

@@ -1,0 +1,424 @@
+// C ABI of the GB300 min-cut solver (declared in include/pog.h) and its host driver:
+// state allocation, the push/relabel <-> global-relabel iteration with its exact
+// termination test (Section 3.2.4), cut extraction and the flow value.
+#include <cstddef>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pog.h"
+#include "pog_internal.cuh"
+#include "pog_launch.h"
+
+using pog::DevCounters;
+using pog::Grid;
+
+namespace {
+
+constexpr int kGapLevels = 1 << 20;          // labels tracked by the gap bitmap
+constexpr int kDefaultSweeps = 16;           // push/relabel sweeps per global relabel
+constexpr int kDefaultOps = 4;               // push/relabel operations per node per sweep
+constexpr int kDefaultMaxRounds = 1 << 20;   // global relabels before giving up
+constexpr int kRelaxPerCheck = 8;            // relaxation passes between host checks
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+pog_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return POG_OK;
+    return e == cudaErrorMemoryAllocation ? POG_E_NOMEM : POG_E_CUDA;
+}
+
+#define POG_TRY_CUDA(expr)                                   \
+    do {                                                     \
+        const pog_status _s = from_cuda((expr));             \
+        if (_s != POG_OK) return _s;                         \
+    } while (0)
+
+#define POG_TRY(expr)                                        \
+    do {                                                     \
+        const pog_status _s = (expr);                        \
+        if (_s != POG_OK) return _s;                         \
+    } while (0)
+
+void set_options(pog_graph *g, const pog_options *opt) {
+    g->sweeps_per_relabel = (opt && opt->sweeps_per_relabel > 0) ? opt->sweeps_per_relabel : kDefaultSweeps;
+    g->max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : kDefaultMaxRounds;
+    g->tile_sweeps = (opt && opt->tile_sweeps > 0) ? opt->tile_sweeps : kDefaultOps;
+    g->flags = opt ? opt->flags : 0;
+}
+
+template <class T>
+pog_status reset_field(pog_graph *g, T DevCounters::*field) {
+    const size_t off = (size_t)((char *)&(g->ctr->*field) - (char *)g->ctr);
+    return from_cuda(cudaMemsetAsync((char *)g->ctr + off, 0, sizeof(T), g->stream));
+}
+
+pog_status read_counters(pog_graph *g) {
+    POG_TRY_CUDA(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, g->stream));
+    POG_TRY_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->ctr_host->error) return POG_E_OVERFLOW;
+    return POG_OK;
+}
+
+enum { ST_BFS = 2, ST_CUT = 3, ST_SWEEP = 1, ST_ROUNDS = 0, ST_GAPS = 4, ST_ACTIVE0 = 5, ST_LAUNCHES = 6 };
+enum { TM_SWEEP = 0, TM_BFS = 1, TM_CUT = 2, TM_BUILD = 3 };
+
+// Launch wrapped in a pair of CUDA events when POG_FLAG_TIMING is set.
+template <class Launch>
+cudaError_t timed(pog_graph *g, int family, Launch launch) {
+    if (!(g->flags & POG_FLAG_TIMING)) return launch();
+    pog_graph::Timer &t = g->timers[family];
+    if (t.used + 2 > t.cap) {
+        const int cap = t.cap ? 2 * t.cap : 256;
+        cudaEvent_t *ev = static_cast<cudaEvent_t *>(std::realloc(t.ev, sizeof(cudaEvent_t) * cap));
+        if (!ev) return cudaErrorMemoryAllocation;
+        for (int i = t.cap; i < cap; ++i) {
+            const cudaError_t e = cudaEventCreate(&ev[i]);
+            if (e != cudaSuccess) {
+                t.ev = ev;
+                t.cap = i;
+                return e;
+            }
+        }
+        t.ev = ev;
+        t.cap = cap;
+    }
+    cudaError_t e = cudaEventRecord(t.ev[t.used], g->stream);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(t.ev[t.used + 1], g->stream);
+    if (e == cudaSuccess) t.used += 2;
+    return e;
+}
+
+// Fold recorded event pairs into milliseconds (the stream must have been synchronised).
+void fold_timers(pog_graph *g) {
+    for (auto &t : g->timers) {
+        for (int i = 0; i + 1 < t.used; i += 2) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, t.ev[i], t.ev[i + 1]) == cudaSuccess) t.ms += ms;
+        }
+        t.used = 0;
+    }
+}
+
+// Relaxation to a fixpoint; `relax` launches one pass and sets ctr->changed on progress.
+template <class Relax>
+pog_status relax_to_fixpoint(pog_graph *g, Relax relax, long long &passes) {
+    const long long limit = g->N + 2 * kRelaxPerCheck;  // a monotone relaxation settles within N passes
+    for (long long done = 0;;) {
+        POG_TRY(reset_field(g, &DevCounters::changed));
+        for (int p = 0; p < kRelaxPerCheck; ++p) POG_TRY_CUDA(relax());
+        g->stats[ST_LAUNCHES] += kRelaxPerCheck;
+        passes += kRelaxPerCheck;
+        done += kRelaxPerCheck;
+        POG_TRY(read_counters(g));
+        if (!g->ctr_host->changed) return POG_OK;
+        if (done > limit) return POG_E_NOCONVERGE;
+    }
+}
+
+pog_status global_relabel(pog_graph *g) {
+    POG_TRY_CUDA(pog::launch_bfs_init(g->grid, g->stream));
+    g->stats[ST_LAUNCHES] += 1;
+    return relax_to_fixpoint(
+        g, [&] { return timed(g, TM_BFS, [&] { return pog::launch_bfs_relax(g->grid, g->stream); }); },
+        g->stats[ST_BFS]);
+}
+
+pog_status count_active(pog_graph *g, long long &active) {
+    POG_TRY(reset_field(g, &DevCounters::active));
+    POG_TRY(reset_field(g, &DevCounters::max_label));
+    POG_TRY_CUDA(pog::launch_count_active(g->grid, g->stream));
+    g->stats[ST_LAUNCHES] += 1;
+    POG_TRY(read_counters(g));
+    active = (long long)g->ctr_host->active;
+    return POG_OK;
+}
+
+unsigned int *gap_bits(pog_graph *g) {
+    // The bitmap sits after the counters in the arena.
+    return reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(g->ctr) + align_up(sizeof(DevCounters), 256));
+}
+
+pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
+    std::memset(g->stats, 0, sizeof g->stats);
+    for (int f = TM_SWEEP; f <= TM_CUT; ++f) g->timers[f].ms = 0.0;
+    POG_TRY(read_counters(g));  // surfaces build errors (cost range)
+    long long active = 0;
+    POG_TRY(global_relabel(g));
+    POG_TRY(count_active(g, active));
+    g->stats[ST_ROUNDS] = 1;
+    g->stats[ST_ACTIVE0] = active;
+    const bool gap = !(g->flags & POG_FLAG_NO_GAP);
+    const int half = g->sweeps_per_relabel / 2;
+    while (active > 0) {
+        if (g->stats[ST_ROUNDS] >= g->max_rounds) return POG_E_NOCONVERGE;
+        for (int k = 0; k < g->sweeps_per_relabel; ++k) {
+            POG_TRY_CUDA(timed(g, TM_SWEEP, [&] { return pog::launch_sweep(g->grid, g->tile_sweeps, g->stream); }));
+            if (gap && k + 1 == half) {
+                POG_TRY(reset_field(g, &DevCounters::raised));
+                POG_TRY(reset_field(g, &DevCounters::max_label));
+                POG_TRY_CUDA(pog::launch_gap(g->grid, gap_bits(g), kGapLevels, g->stream));
+                g->stats[ST_LAUNCHES] += 3;
+                g->stats[ST_GAPS]++;
+            }
+        }
+        g->stats[ST_SWEEP] += g->sweeps_per_relabel;
+        g->stats[ST_LAUNCHES] += g->sweeps_per_relabel;
+        POG_TRY(global_relabel(g));
+        POG_TRY(count_active(g, active));
+        g->stats[ST_ROUNDS]++;
+    }
+    // Maximum preflow reached: extract the minimal cut, the heights and the flow value.
+    POG_TRY_CUDA(pog::launch_cut_init(g->grid, g->stream));
+    g->stats[ST_LAUNCHES] += 4;  // cut init, heights, excess sum, and the build's two kernels - 1
+    POG_TRY(relax_to_fixpoint(
+        g, [&] { return timed(g, TM_CUT, [&] { return pog::launch_cut_relax(g->grid, g->stream); }); },
+        g->stats[ST_CUT]));
+    POG_TRY_CUDA(pog::launch_heights(g->grid, g->heights, g->stream));
+    POG_TRY(reset_field(g, &DevCounters::excess_sum));
+    POG_TRY_CUDA(pog::launch_excess_sum(g->grid, g->stream));
+    POG_TRY(read_counters(g));
+    const DevCounters &c = *g->ctr_host;
+    g->flow = (long long)c.bottom_const + (long long)c.src_total - (long long)c.excess_sum;
+    fold_timers(g);
+    g->solved = 1;
+    *flow_out = g->flow;
+    return POG_OK;
+}
+
+template <class Launch>
+pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha, const pog_options *opt,
+                      void *stream, pog_graph **out, Launch launch) {
+    if (!out || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 || alpha >= (1 << 30)) return POG_E_INVALID;
+    const long long N = (long long)X * Y * Z;
+    if (N >= (1ll << 31) - 64) return POG_E_INVALID;
+    pog_graph *g = new (std::nothrow) pog_graph();
+    if (!g) return POG_E_NOMEM;
+    g->X = X;
+    g->Y = Y;
+    g->Z = Z;
+    g->delta = delta;
+    g->alpha = alpha;
+    g->N = N;
+    g->stream = static_cast<cudaStream_t>(stream);
+    set_options(g, opt);
+    const int arrays = alpha > 0 ? 10 : 8;
+    const size_t per = align_up((size_t)N * sizeof(int32_t), 256);
+    const size_t heights = align_up((size_t)X * Y * sizeof(int32_t), 256);
+    const size_t ctr = align_up(sizeof(DevCounters), 256) + (size_t)kGapLevels / 8;
+    g->arena_bytes = per * arrays + heights + ctr;
+    cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return e == cudaErrorMemoryAllocation ? POG_E_NOMEM : POG_E_CUDA;
+    }
+    e = cudaHostAlloc(reinterpret_cast<void **>(&g->ctr_host), sizeof(DevCounters), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaFree(g->arena);
+        delete g;
+        return POG_E_NOMEM;
+    }
+    char *p = static_cast<char *>(g->arena);
+    Grid &gr = g->grid;
+    gr.X = X;
+    gr.Y = Y;
+    gr.Z = Z;
+    gr.delta = delta;
+    gr.alpha = alpha;
+    gr.N = (int)N;
+    int32_t **slots[10] = {&gr.lab, &gr.exc, &gr.snk, &gr.fdn, &gr.fh[0], &gr.fh[1], &gr.fh[2], &gr.fh[3],
+                           &gr.gs[0], &gr.gs[1]};
+    for (int i = 0; i < 10; ++i) {
+        *slots[i] = i < arrays ? reinterpret_cast<int32_t *>(p) : nullptr;
+        if (i < arrays) p += per;
+    }
+    g->heights = reinterpret_cast<int32_t *>(p);
+    p += heights;
+    g->ctr = reinterpret_cast<DevCounters *>(p);
+    gr.ctr = g->ctr;
+    e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
+    if (e == cudaSuccess) e = timed(g, TM_BUILD, [&] { return launch(gr, g->stream); });
+    if (e != cudaSuccess) {
+        pog_free(g);
+        return from_cuda(e);
+    }
+    *out = g;
+    return POG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pog_status pog_build(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha,
+                     const pog_options *opt, void *stream, pog_graph **out) {
+    if (!cost_dev) return POG_E_INVALID;
+    return build_impl(X, Y, Z, delta, alpha, opt, stream, out,
+                      [&](const Grid &g, cudaStream_t st) { return pog::launch_build_i32(g, cost_dev, st); });
+}
+
+pog_status pog_build_f32(const float *cost_dev, float scale, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                         int32_t alpha, const pog_options *opt, void *stream, pog_graph **out) {
+    if (!cost_dev || !(scale > 0.0f)) return POG_E_INVALID;
+    return build_impl(X, Y, Z, delta, alpha, opt, stream, out, [&](const Grid &g, cudaStream_t st) {
+        return pog::launch_build_f32(g, cost_dev, scale, nullptr, 0, st);
+    });
+}
+
+pog_status pog_build_f32_augmented(const float *cost_dev, float scale, const int32_t *h_aug_dev, int32_t margin,
+                                   int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha,
+                                   const pog_options *opt, void *stream, pog_graph **out) {
+    if (!cost_dev || !h_aug_dev || !(scale > 0.0f) || margin < 0 || margin >= (1 << 28)) return POG_E_INVALID;
+    return build_impl(X, Y, Z, delta, alpha, opt, stream, out, [&](const Grid &g, cudaStream_t st) {
+        return pog::launch_build_f32(g, cost_dev, scale, h_aug_dev, margin, st);
+    });
+}
+
+pog_status pog_energy(const pog_graph *g, int64_t *energy_out) {
+    if (!g || !energy_out) return POG_E_INVALID;
+    if (!g->solved) return POG_E_STATE;
+    // max-flow = E*(h) + K with K = -1 - sum_col c(col,0) + sum_{w<0} (-w) (the cut of
+    // the closed set below h, Eq. 6, after the weights telescope along each column).
+    const DevCounters &c = *g->ctr_host;
+    const long long K = -1 - (long long)c.bottom_sum + (long long)c.src_total + (long long)c.neg_bottom;
+    *energy_out = g->flow - K;
+    return POG_OK;
+}
+
+pog_status pog_surface_energy(const float *cost_dev, float scale, const int32_t *h_dev, int32_t B, int32_t X,
+                              int32_t Y, int32_t Z, int32_t alpha, int64_t *energy_dev, void *stream) {
+    if (!cost_dev || !h_dev || !energy_dev || !(scale > 0.0f) || B < 0 || X < 1 || Y < 1 || Z < 1 || alpha < 0)
+        return POG_E_INVALID;
+    if (B == 0) return POG_OK;
+    return from_cuda(pog::launch_surface_energy(cost_dev, scale, h_dev, B, X, Y, Z, alpha,
+                                                reinterpret_cast<long long *>(energy_dev),
+                                                static_cast<cudaStream_t>(stream)));
+}
+
+pog_status pog_maxflow(pog_graph *g, int64_t *flow_out) {
+    if (!g || !flow_out) return POG_E_INVALID;
+    g->solved = 0;
+    return maxflow_impl(g, flow_out);
+}
+
+pog_status pog_surface(pog_graph *g, int32_t *heights_dev) {
+    if (!g || !heights_dev) return POG_E_INVALID;
+    if (!g->solved) return POG_E_STATE;
+    return from_cuda(cudaMemcpyAsync(heights_dev, g->heights, sizeof(int32_t) * (size_t)g->X * g->Y,
+                                     cudaMemcpyDeviceToDevice, g->stream));
+}
+
+pog_status pog_stats(const pog_graph *g, pog_stats_t *out) {
+    if (!g || !out) return POG_E_INVALID;
+    std::memset(out, 0, sizeof *out);
+    out->rounds = g->stats[ST_ROUNDS];
+    out->sweeps = g->stats[ST_SWEEP];
+    out->bfs_passes = g->stats[ST_BFS];
+    out->cut_passes = g->stats[ST_CUT];
+    out->gaps = g->stats[ST_GAPS];
+    out->active_initial = g->stats[ST_ACTIVE0];
+    out->launches = g->stats[ST_LAUNCHES] + 1;
+    out->nodes = g->N;
+    out->state_bytes = (long long)g->arena_bytes;
+    if (g->timers[TM_BUILD].used) {  // the build was timed; its events are complete after pog_maxflow
+        if (cudaStreamSynchronize(g->stream) != cudaSuccess) return POG_E_CUDA;
+        fold_timers(const_cast<pog_graph *>(g));
+    }
+    out->sweep_ms = g->timers[TM_SWEEP].ms;
+    out->bfs_ms = g->timers[TM_BFS].ms;
+    out->cut_ms = g->timers[TM_CUT].ms;
+    out->build_ms = g->timers[TM_BUILD].ms;
+    return POG_OK;
+}
+
+pog_status pog_export_state(const pog_graph *g, int32_t *excess, int32_t *sink, int32_t *fdown, int32_t *fhard,
+                            int32_t *gsoft, int32_t *in_cut) {
+    if (!g) return POG_E_INVALID;
+    if (!g->solved) return POG_E_STATE;
+    const size_t bytes = sizeof(int32_t) * (size_t)g->N;
+    struct {
+        int32_t *dst;
+        const int32_t *src;
+    } copies[10] = {{excess, g->grid.exc}, {sink, g->grid.snk}, {fdown, g->grid.fdn}, {in_cut, g->grid.lab}};
+    int n = 4;
+    for (int d = 0; d < 4; ++d) copies[n++] = {fhard ? fhard + d * g->N : nullptr, g->grid.fh[d]};
+    if (g->alpha > 0)
+        for (int k = 0; k < 2; ++k) copies[n++] = {gsoft ? gsoft + k * g->N : nullptr, g->grid.gs[k]};
+    for (int i = 0; i < n; ++i)
+        if (copies[i].dst)
+            POG_TRY_CUDA(cudaMemcpyAsync(copies[i].dst, copies[i].src, bytes, cudaMemcpyDeviceToHost, g->stream));
+    POG_TRY_CUDA(cudaStreamSynchronize(g->stream));
+    return POG_OK;
+}
+
+void pog_free(pog_graph *g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    for (auto &t : g->timers) {
+        for (int i = 0; i < t.cap; ++i) cudaEventDestroy(t.ev[i]);
+        std::free(t.ev);
+    }
+    cudaFree(g->arena);
+    cudaFreeHost(g->ctr_host);
+    delete g;
+}
+
+const char *pog_strerror(pog_status s) {
+    switch (s) {
+        case POG_OK: return "ok";
+        case POG_E_INVALID: return "invalid argument";
+        case POG_E_OVERFLOW: return "value out of the int32 range (cost magnitude or arc flow)";
+        case POG_E_NOMEM: return "out of memory";
+        case POG_E_CUDA: return "CUDA runtime error";
+        case POG_E_NOCONVERGE: return "iteration cap reached before convergence";
+        case POG_E_TIMEOUT: return "bounded device wait timed out";
+        case POG_E_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+pog_status pog_quantise(const float *in_dev, int32_t *out_dev, int64_t n, float scale, void *stream) {
+    if (n < 0 || (n > 0 && (!in_dev || !out_dev)) || !(scale > 0.0f)) return POG_E_INVALID;
+    if (n == 0) return POG_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    POG_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&err), sizeof(int), st));
+    int host_err = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = pog::launch_quantise(in_dev, out_dev, n, scale, err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(err, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    return host_err ? POG_E_OVERFLOW : POG_OK;
+}
+
+pog_status pog_backward(float *grad_dev, const int32_t *h_dev, const int32_t *h_target_dev, const int32_t *h_hat_dev,
+                        const float *g_energy_dev, const float *g_hinge_dev, int32_t B, int32_t X, int32_t Y,
+                        int32_t Z, void *stream) {
+    if (!grad_dev || !h_dev || !g_energy_dev || B < 0 || X < 1 || Y < 1 || Z < 1) return POG_E_INVALID;
+    if (g_hinge_dev && (!h_target_dev || !h_hat_dev)) return POG_E_INVALID;
+    if (B == 0) return POG_OK;
+    return from_cuda(pog::launch_backward(grad_dev, h_dev, h_target_dev, h_hat_dev, g_energy_dev, g_hinge_dev, B,
+                                          X * Y, Z, static_cast<cudaStream_t>(stream)));
+}
+
+pog_status pog_solve_batch(int32_t n, const pog_volume *vols, const pog_options *opt, void *stream,
+                           int64_t *flows_out, int32_t *const *heights_dev) {
+    if (n < 0 || (n > 0 && (!vols || !flows_out || !heights_dev))) return POG_E_INVALID;
+    pog_status first = POG_OK;
+    for (int i = 0; i < n; ++i) {
+        pog_graph *g = nullptr;
+        const pog_volume &v = vols[i];
+        pog_status s = pog_build(v.cost_dev, v.X, v.Y, v.Z, v.delta, v.alpha, opt, stream, &g);
+        if (s == POG_OK) s = pog_maxflow(g, &flows_out[i]);
+        if (s == POG_OK) s = pog_surface(g, heights_dev[i]);
+        pog_free(g);
+        if (s != POG_OK && first == POG_OK) first = s;
+    }
+    return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,491 @@
+// Node-parallel kernels of the GB300 min-cut solver: graph construction, push/relabel
+// sweeps, global relabelling by reverse BFS, gap relabelling, termination counts, cut
+// extraction, surface heights, quantisation and the energy backward.
+#include "pog_internal.cuh"
+#include "pog_launch.h"
+
+namespace pog {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of a 64-bit value, added once per block into *dst.
+__device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned long long *dst) {
+    __shared__ unsigned long long part[kThreads / 32];
+    v = warp_sum_u64(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? part[lane] : 0ull;
+        v = warp_sum_u64(v);
+        if (lane == 0 && v != 0ull) atomicAdd(dst, v);
+    }
+}
+
+inline int blocks_for(long long n) { return (int)((n + kThreads - 1) / kThreads); }
+
+// ----------------------------------------------------------------------------------
+// Graph construction (Section 1.2): node weights w(z) = c(z) - c(z-1) become source
+// excess (w < 0) or sink residual (w > 0); arcs start empty; labels start at 0.
+// ----------------------------------------------------------------------------------
+
+struct CostI32 {
+    const int32_t *c;
+    __device__ __forceinline__ int load(int i, int &err) const {
+        const int v = c[i];
+        if (v >= (1 << 30) || v <= -(1 << 30)) err |= POG_ERR_COST_RANGE;
+        return v;
+    }
+};
+
+struct CostF32 {
+    const float *c;
+    float scale;
+    const int32_t *h_aug;  // optional surface whose nodes get `margin` added
+    int margin;
+    int Z;
+    __device__ __forceinline__ int load(int i, int &err) const {
+        const float v = c[i] * scale;  // exact for a power-of-two scale
+        if (!(fabsf(v) < 1073741824.0f)) {  // also rejects NaN / Inf
+            err |= POG_ERR_COST_RANGE;
+            return 0;
+        }
+        int q = __float2int_rn(v);  // round half to even
+        if (h_aug && h_aug[i / Z] == i % Z) q += margin;
+        return q;
+    }
+};
+
+template <class Cost>
+__global__ void k_build(Grid g, Cost cost) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long src = 0, bsum = 0, bpos = 0, bneg = 0;
+    int err = 0;
+    if (u < g.N) {
+        const int z = u % g.Z;
+        const int c = cost.load(u, err);
+        int e = 0, s = 0, l = POG_INF;
+        if (z == 0) {
+            bsum = (unsigned long long)(long long)c;
+            if (u != 0 && c > 0) bpos = (unsigned long long)c;
+            if (u != 0 && c < 0) bneg = (unsigned long long)(-(long long)c);
+        } else {
+            const int w = c - cost.load(u - 1, err);
+            e = w < 0 ? -w : 0;
+            s = w > 0 ? w : 0;
+            l = 0;
+            src = (unsigned long long)e;
+        }
+        g.lab[u] = l;
+        g.exc[u] = e;
+        g.snk[u] = s;
+        g.fdn[u] = 0;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) g.fh[d][u] = 0;
+        if (g.gs[0]) {
+            g.gs[0][u] = 0;
+            g.gs[1][u] = 0;
+        }
+    }
+    if (err) atomicOr(&g.ctr->error, err);
+    block_add_u64(src, &g.ctr->src_total);
+    __syncthreads();
+    block_add_u64(bsum, &g.ctr->bottom_sum);
+    __syncthreads();
+    block_add_u64(bpos, &g.ctr->pos_bottom);
+    __syncthreads();
+    block_add_u64(bneg, &g.ctr->neg_part);
+}
+
+// The bottom node of column (0,0) carries the offset -(1 + sum c(., ., 0)); the bottom
+// layer's sink arcs give a constant part of the flow value.
+template <class Cost>
+__global__ void k_bottom_const(Grid g, Cost cost) {
+    int err = 0;
+    const long long c00 = cost.load(0, err);
+    const long long w00 = c00 - 1 - (long long)g.ctr->bottom_sum;
+    g.ctr->bottom_const = g.ctr->pos_bottom + (unsigned long long)(w00 > 0 ? w00 : 0);
+    g.ctr->neg_bottom = g.ctr->neg_part + (unsigned long long)(w00 < 0 ? -w00 : 0);
+}
+
+// ----------------------------------------------------------------------------------
+// Push/relabel sweep (Section 2.1, Algorithm 2), lock-free: each node is discharged
+// only by its own thread; neighbours' excess and the paired arc values are changed
+// with atomics. Every value a thread reads can only move, concurrently, in the
+// direction that makes its push smaller than allowed, so stale reads are safe.
+// ----------------------------------------------------------------------------------
+
+template <bool SOFT>
+__global__ void k_push_relabel(Grid g, int ops) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.N) return;
+    const int z = u % g.Z;
+    if (z == 0) return;
+    const int col = u / g.Z;
+    const int x = col / g.Y, y = col - x * g.Y;
+    for (int it = 0; it < ops; ++it) {
+        const int e = ldcg(g.exc + u);
+        const int h = ldcg(g.lab + u);
+        if (e <= 0 || h >= POG_INF) return;
+        int best = POG_INF, kind = ARC_NONE, dir = 0, target = -1, res = 0;
+        const int s = ldcg(g.snk + u);
+        if (s > 0) {
+            best = 0;
+            kind = ARC_SINK;
+            res = s;
+        } else {
+            for_each_residual_arc<SOFT>(g, u, x, y, z, [&](int k, int d, int v, int r) {
+                const int l = ldcg(g.lab + v);
+                if (l < best) {
+                    best = l;
+                    kind = k;
+                    dir = d;
+                    target = v;
+                    res = r;
+                }
+            });
+        }
+        if (kind != ARC_NONE && h > best) {
+            const int delta = e < res ? e : res;
+            int sat = 0;
+            switch (kind) {
+                case ARC_SINK: g.snk[u] = s - delta; break;
+                case ARC_DOWN: sat = atomicAdd(g.fdn + u, delta) + delta == POG_CAP_INF; break;
+                case ARC_UP: atomicSub(g.fdn + u + 1, delta); break;
+                case ARC_HOUT: sat = atomicAdd(g.fh[dir] + u, delta) + delta == POG_CAP_INF; break;
+                case ARC_HIN: atomicSub(g.fh[dir ^ 1] + target, delta); break;
+                default:
+                    if (dir & 1) atomicAdd(g.gs[dir >> 1] + u, delta);
+                    else atomicSub(g.gs[dir >> 1] + target, delta);
+                    break;
+            }
+            atomicSub(g.exc + u, delta);
+            if (kind != ARC_SINK) {
+                const int old = atomicAdd(g.exc + target, delta);
+                if (old > 0x7fffffff - delta) sat = 1;
+            }
+            if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
+        } else {
+            g.lab[u] = best >= POG_INF - 1 ? POG_INF : best + 1;  // relabel
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// Global relabelling (Section 3.2.2, Algorithm 3): exact distances to the sink in the
+// residual graph. Level 1 holds the nodes whose sink arc is residual. A relaxation
+// pass lowers d(u) to min over residual arcs (u, v) of d(v) + 1; labels only decrease
+// and each is the length of a real path, so the fixpoint is the BFS distance; nodes
+// that never get a finite value cannot reach t (the gap effect, Section 2.1).
+// ----------------------------------------------------------------------------------
+
+__global__ void k_bfs_init(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.N) return;
+    const int z = u % g.Z;
+    g.lab[u] = (z != 0 && g.snk[u] > 0) ? 1 : POG_INF;
+}
+
+template <bool SOFT>
+__global__ void k_bfs_relax(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.N) return;
+    const int z = u % g.Z;
+    if (z == 0) return;
+    const int h = ldcg(g.lab + u);
+    if (h <= 1) return;
+    const int col = u / g.Z;
+    const int x = col / g.Y, y = col - x * g.Y;
+    int best = h;
+    for_each_residual_arc<SOFT>(g, u, x, y, z, [&](int, int, int v, int) {
+        const int l = ldcg(g.lab + v) + 1;
+        if (l < best) best = l;
+    });
+    if (best < h) {
+        g.lab[u] = best;
+        g.ctr->changed = 1;
+    }
+}
+
+// Active nodes (excess > 0, finite label) and the largest finite label.
+__global__ void k_count_active(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long a = 0;
+    int lmax = 0;
+    if (u < g.N && u % g.Z != 0) {
+        const int l = g.lab[u];
+        if (l < POG_INF) {
+            lmax = l;
+            if (g.exc[u] > 0) a = 1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0 && lmax > 0) atomicMax(&g.ctr->max_label, lmax);
+    block_add_u64(a, &g.ctr->active);
+}
+
+// ----------------------------------------------------------------------------------
+// Gap relabelling (Section 2.1): if no node has label g while some have g < d < INF,
+// those cannot reach t and are raised to INF. Level occupancy is a bitmap.
+// ----------------------------------------------------------------------------------
+
+__global__ void k_gap_occupancy(Grid g, unsigned int *bits, int levels) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int lmax = 0;
+    if (u < g.N && u % g.Z != 0) {
+        const int l = g.lab[u];
+        if (l < levels) atomicOr(bits + (l >> 5), 1u << (l & 31));
+        if (l < POG_INF) lmax = l;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0 && lmax > 0) atomicMax(&g.ctr->max_label, lmax);
+}
+
+// One block: the first empty level above 0 that lies below the largest finite label.
+__global__ void k_gap_find(Grid g, const unsigned int *bits, int levels) {
+    __shared__ int first;
+    if (threadIdx.x == 0) first = 0x7fffffff;
+    __syncthreads();
+    const int lmax = min(g.ctr->max_label, levels - 1);
+    for (int w = threadIdx.x; w * 32 <= lmax; w += blockDim.x) {
+        unsigned int empty = ~bits[w];
+        if (w == 0) empty &= ~1u;  // level 0 is the sink itself
+        if (empty) {
+            const int l = w * 32 + __ffs(empty) - 1;
+            if (l < lmax) atomicMin(&first, l);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) g.ctr->gap_level = first == 0x7fffffff ? 0 : first;
+}
+
+__global__ void k_gap_raise(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gap = g.ctr->gap_level;
+    unsigned long long r = 0;
+    if (gap > 0 && u < g.N && u % g.Z != 0) {
+        const int l = g.lab[u];
+        if (l > gap && l < POG_INF) {
+            g.lab[u] = POG_INF;
+            r = 1;
+        }
+    }
+    block_add_u64(r, &g.ctr->raised);
+}
+
+// ----------------------------------------------------------------------------------
+// Cut extraction: the source side of the minimal minimum cut is the set of nodes
+// reachable in the residual graph from s and from every node with excess (the bottom
+// layer is part of s and has no residual arc out). Marks live in the label array.
+// ----------------------------------------------------------------------------------
+
+__global__ void k_cut_init(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.N) return;
+    g.lab[u] = (u % g.Z != 0 && g.exc[u] > 0) ? 1 : 0;
+}
+
+template <bool SOFT>
+__global__ void k_cut_relax(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.N) return;
+    const int z = u % g.Z;
+    if (z == 0 || ldcg(g.lab + u) == 0) return;
+    const int col = u / g.Z;
+    const int x = col / g.Y, y = col - x * g.Y;
+    bool any = false;
+    for_each_residual_arc<SOFT>(g, u, x, y, z, [&](int, int, int v, int) {
+        if (ldcg(g.lab + v) == 0) {
+            g.lab[v] = 1;
+            any = true;
+        }
+    });
+    if (any) g.ctr->changed = 1;
+}
+
+// One warp per column: the top marked node (0 when only the bottom layer is in S).
+__global__ void k_heights(Grid g, int32_t *heights) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int cols = g.X * g.Y;
+    if (warp >= cols) return;
+    const int32_t *m = g.lab + (long long)warp * g.Z;
+    int top = 0;
+    for (int z0 = 0; z0 < g.Z; z0 += 32) {
+        const int z = z0 + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, z >= 1 && z < g.Z && m[z] != 0);
+        if (b) top = z0 + 31 - __clz(b);
+    }
+    if (lane == 0) heights[warp] = top;
+}
+
+__global__ void k_excess_sum(Grid g) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long e = 0;
+    if (u < g.N && u % g.Z != 0) e = (unsigned long long)(long long)g.exc[u];
+    block_add_u64(e, &g.ctr->excess_sum);
+}
+
+// ----------------------------------------------------------------------------------
+// Quantisation and the energy backward.
+// ----------------------------------------------------------------------------------
+
+__global__ void k_quantise(const float *in, int32_t *out, long long n, float scale, int *err) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = in[i] * scale;
+    if (!(fabsf(v) < 1073741824.0f)) {
+        atomicOr(err, POG_ERR_COST_RANGE);
+        out[i] = 0;
+        return;
+    }
+    out[i] = __float2int_rn(v);
+}
+
+// grad = g_e * onehot(h) + g_h * (onehot(h_target) - onehot(h_hat)); each thread writes
+// four consecutive z of one column (vectorised when Z is a multiple of 4).
+__global__ void k_backward(float *grad, const int32_t *h, const int32_t *ht, const int32_t *hh,
+                           const float *ge, const float *gh, int B, int XY, int Z) {
+    const long long n = (long long)B * XY * Z;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i >= n) return;
+    for (int k = 0; k < 4 && i + k < n; ++k) {
+        const long long e = i + k;
+        const long long colg = e / Z;  // b * XY + col
+        const int z = (int)(e - colg * Z);
+        const int b = (int)(colg / XY);
+        float v = (h[colg] == z) ? ge[b] : 0.0f;
+        if (gh) {
+            const float s = gh[b];
+            if (ht[colg] == z) v += s;
+            if (hh[colg] == z) v -= s;
+        }
+        grad[e] = v;
+    }
+}
+
+// Surface energy of Eq. 1 on the quantised costs, one block per volume:
+// sum_col cq(col, h) + alpha * sum over unordered 4-neighbour pairs |h_p - h_q|.
+__global__ void k_surface_energy(const float *cost, float scale, const int32_t *h, int X, int Y, int Z, int alpha,
+                                 long long *out) {
+    const int b = blockIdx.x;
+    const int XY = X * Y;
+    const float *c = cost + (long long)b * XY * Z;
+    const int32_t *hb = h + (long long)b * XY;
+    unsigned long long acc = 0;
+    int bad = 0;
+    for (int col = threadIdx.x; col < XY; col += blockDim.x) {
+        const int x = col / Y, y = col - x * Y;
+        const int hp = hb[col];
+        if (hp < 0 || hp >= Z) {  // not a surface: reported as INT64_MIN
+            bad = 1;
+            continue;
+        }
+        long long e = __float2int_rn(c[(long long)col * Z + hp] * scale);
+        if (x + 1 < X) e += (long long)alpha * abs(hp - hb[col + Y]);
+        if (y + 1 < Y) e += (long long)alpha * abs(hp - hb[col + 1]);
+        acc += (unsigned long long)e;
+    }
+    __shared__ unsigned long long part[kThreads / 32];
+    __shared__ int any_bad;
+    if (threadIdx.x == 0) any_bad = 0;
+    __syncthreads();
+    if (bad) any_bad = 1;
+    acc = warp_sum_u64(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        out[b] = any_bad ? (long long)0x8000000000000000ull : (long long)t;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------- launchers
+
+#define POG_LAUNCH(kernel, n, stream, ...)                                          \
+    do {                                                                            \
+        kernel<<<blocks_for(n), kThreads, 0, stream>>>(__VA_ARGS__);                \
+        return cudaGetLastError();                                                  \
+    } while (0)
+
+cudaError_t launch_build_i32(const Grid &g, const int32_t *cost, cudaStream_t st) {
+    CostI32 c{cost};
+    k_build<<<blocks_for(g.N), kThreads, 0, st>>>(g, c);
+    k_bottom_const<<<1, 1, 0, st>>>(g, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_f32(const Grid &g, const float *cost, float scale, const int32_t *h_aug, int margin,
+                             cudaStream_t st) {
+    CostF32 c{cost, scale, h_aug, margin, g.Z};
+    k_build<<<blocks_for(g.N), kThreads, 0, st>>>(g, c);
+    k_bottom_const<<<1, 1, 0, st>>>(g, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const Grid &g, int ops, cudaStream_t st) {
+    if (g.gs[0]) POG_LAUNCH(k_push_relabel<true>, g.N, st, g, ops);
+    POG_LAUNCH(k_push_relabel<false>, g.N, st, g, ops);
+}
+
+cudaError_t launch_bfs_init(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_bfs_init, g.N, st, g); }
+
+cudaError_t launch_bfs_relax(const Grid &g, cudaStream_t st) {
+    if (g.gs[0]) POG_LAUNCH(k_bfs_relax<true>, g.N, st, g);
+    POG_LAUNCH(k_bfs_relax<false>, g.N, st, g);
+}
+
+cudaError_t launch_count_active(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_count_active, g.N, st, g); }
+
+cudaError_t launch_gap(const Grid &g, unsigned int *bits, int levels, cudaStream_t st) {
+    cudaMemsetAsync(bits, 0, (size_t)(levels / 32) * sizeof(unsigned int), st);
+    k_gap_occupancy<<<blocks_for(g.N), kThreads, 0, st>>>(g, bits, levels);
+    k_gap_find<<<1, 1024, 0, st>>>(g, bits, levels);
+    k_gap_raise<<<blocks_for(g.N), kThreads, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cut_init(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_cut_init, g.N, st, g); }
+
+cudaError_t launch_cut_relax(const Grid &g, cudaStream_t st) {
+    if (g.gs[0]) POG_LAUNCH(k_cut_relax<true>, g.N, st, g);
+    POG_LAUNCH(k_cut_relax<false>, g.N, st, g);
+}
+
+cudaError_t launch_heights(const Grid &g, int32_t *heights, cudaStream_t st) {
+    const long long threads = (long long)g.X * g.Y * 32;
+    POG_LAUNCH(k_heights, threads, st, g, heights);
+}
+
+cudaError_t launch_excess_sum(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_excess_sum, g.N, st, g); }
+
+cudaError_t launch_quantise(const float *in, int32_t *out, long long n, float scale, int *err, cudaStream_t st) {
+    POG_LAUNCH(k_quantise, n, st, in, out, n, scale, err);
+}
+
+cudaError_t launch_backward(float *grad, const int32_t *h, const int32_t *ht, const int32_t *hh, const float *ge,
+                            const float *gh, int B, int XY, int Z, cudaStream_t st) {
+    const long long n = ((long long)B * XY * Z + 3) / 4;
+    POG_LAUNCH(k_backward, n, st, grad, h, ht, hh, ge, gh, B, XY, Z);
+}
+
+cudaError_t launch_surface_energy(const float *cost, float scale, const int32_t *h, int B, int X, int Y, int Z,
+                                  int alpha, long long *out, cudaStream_t st) {
+    k_surface_energy<<<B, kThreads, 0, st>>>(cost, scale, h, X, Y, Z, alpha, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pog
