@@ -203,7 +203,7 @@ def run_ours(args):
     e2e_value = ws * N * args.steps / (e2e_ms / 1e3) / 1e6
     # roofline of the dominant kernel family, timed live with events on the solve stream
     bytes_per, S = algorithmic_bytes(N, vol.alpha)
-    fam = {"sweep": ("sweep_ms", "sweeps"), "bfs": ("bfs_ms", "bfs_passes"), "cut": ("cut_ms", "cut_passes"),
+    fam = {"sweep": ("sweep_ms", "sweeps"), "bfs": ("bfs_ms", "rounds"), "cut": ("cut_ms", None),
            "build": ("build_ms", None)}
     tot = {k: sum(s[v[0]] for s in stats) for k, v in fam.items()}
     launches = {k: (sum(s[v[1]] for s in stats) if v[1] else len(stats)) for k, v in fam.items()}

@@ -62,11 +62,13 @@ typedef struct {
     int32_t max_rounds;         /* cap on global-relabel rounds before POG_E_NOCONVERGE */
     int32_t tile_sweeps;        /* local sweeps a thread block runs on its shared-memory tile */
     int32_t flags;              /* POG_FLAG_* bits */
-    int32_t reserved[4];
+    int32_t bfs_blocks_per_sm;  /* resident blocks per SM of the cooperative BFS launches */
+    int32_t reserved[3];
 } pog_options;
 
-#define POG_FLAG_NO_GAP 1 /* disable the gap heuristic between global relabels */
-#define POG_FLAG_TIMING 2 /* time each kernel family with CUDA events on the graph's stream */
+#define POG_FLAG_NO_GAP 1     /* disable the gap heuristic between global relabels */
+#define POG_FLAG_TIMING 2     /* time each kernel family with CUDA events on the graph's stream */
+#define POG_FLAG_NO_PREPUSH 4 /* skip the column pre-push along the down arcs */
 
 /* Counters of the last pog_maxflow. */
 typedef struct {
@@ -163,6 +165,17 @@ POG_API pog_status pog_surface_energy(const float *cost_dev, float scale, const 
 
 /* Counters of the last pog_maxflow. out: host. */
 POG_API pog_status pog_stats(const pog_graph *g, pog_stats_t *out);
+
+/*
+ * Diagnostics: the per-level trace of the last global relabel (reverse BFS, Algorithm 3).
+ *   out        : host int64 [3 * max_levels]; entry i holds (frontier size, mode, device
+ *                time in ns) of level i+1, mode 0 = top-down queue expansion, 1 =
+ *                bottom-up scan; the final entry has mode -1 and marks the end time.
+ *   levels_out : host, receives the number of entries written (0 if more than
+ *                min(max_levels, 4096) levels ran).
+ * Synchronises the graph's stream.
+ */
+POG_API pog_status pog_trace(const pog_graph *g, int64_t *out, int32_t max_levels, int32_t *levels_out);
 
 /*
  * Download the residual state after pog_maxflow, for host-side certificates.

@@ -19,7 +19,6 @@ constexpr int kGapLevels = 1 << 20;          // labels tracked by the gap bitmap
 constexpr int kDefaultSweeps = 16;           // push/relabel sweeps per global relabel
 constexpr int kDefaultOps = 4;               // push/relabel operations per node per sweep
 constexpr int kDefaultMaxRounds = 1 << 20;   // global relabels before giving up
-constexpr int kRelaxPerCheck = 8;            // relaxation passes between host checks
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -45,6 +44,7 @@ void set_options(pog_graph *g, const pog_options *opt) {
     g->max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : kDefaultMaxRounds;
     g->tile_sweeps = (opt && opt->tile_sweeps > 0) ? opt->tile_sweeps : kDefaultOps;
     g->flags = opt ? opt->flags : 0;
+    g->bfs_blocks = (opt && opt->bfs_blocks_per_sm > 0) ? opt->bfs_blocks_per_sm : 0;
 }
 
 template <class T>
@@ -56,6 +56,7 @@ pog_status reset_field(pog_graph *g, T DevCounters::*field) {
 pog_status read_counters(pog_graph *g) {
     POG_TRY_CUDA(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, g->stream));
     POG_TRY_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->ctr_host->error & POG_ERR_TIMEOUT) return POG_E_TIMEOUT;
     if (g->ctr_host->error) return POG_E_OVERFLOW;
     return POG_OK;
 }
@@ -101,36 +102,16 @@ void fold_timers(pog_graph *g) {
     }
 }
 
-// Relaxation to a fixpoint; `relax` launches one pass and sets ctr->changed on progress.
-template <class Relax>
-pog_status relax_to_fixpoint(pog_graph *g, Relax relax, long long &passes) {
-    const long long limit = g->N + 2 * kRelaxPerCheck;  // a monotone relaxation settles within N passes
-    for (long long done = 0;;) {
-        POG_TRY(reset_field(g, &DevCounters::changed));
-        for (int p = 0; p < kRelaxPerCheck; ++p) POG_TRY_CUDA(relax());
-        g->stats[ST_LAUNCHES] += kRelaxPerCheck;
-        passes += kRelaxPerCheck;
-        done += kRelaxPerCheck;
-        POG_TRY(read_counters(g));
-        if (!g->ctr_host->changed) return POG_OK;
-        if (done > limit) return POG_E_NOCONVERGE;
-    }
-}
-
-pog_status global_relabel(pog_graph *g) {
-    POG_TRY_CUDA(pog::launch_bfs_init(g->grid, g->stream));
-    g->stats[ST_LAUNCHES] += 1;
-    return relax_to_fixpoint(
-        g, [&] { return timed(g, TM_BFS, [&] { return pog::launch_bfs_relax(g->grid, g->stream); }); },
-        g->stats[ST_BFS]);
-}
-
-pog_status count_active(pog_graph *g, long long &active) {
+// Global relabel (exact reverse BFS from t, one cooperative launch) fused with the
+// termination count; returns the number of active nodes.
+pog_status global_relabel(pog_graph *g, long long &active) {
     POG_TRY(reset_field(g, &DevCounters::active));
-    POG_TRY(reset_field(g, &DevCounters::max_label));
-    POG_TRY_CUDA(pog::launch_count_active(g->grid, g->stream));
+    POG_TRY_CUDA(timed(g, TM_BFS, [&] {
+        return pog::launch_global_relabel(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
+    }));
     g->stats[ST_LAUNCHES] += 1;
     POG_TRY(read_counters(g));
+    g->stats[ST_BFS] += g->ctr_host->max_label;  // BFS levels of this relabel
     active = (long long)g->ctr_host->active;
     return POG_OK;
 }
@@ -145,8 +126,11 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
     for (int f = TM_SWEEP; f <= TM_CUT; ++f) g->timers[f].ms = 0.0;
     POG_TRY(read_counters(g));  // surfaces build errors (cost range)
     long long active = 0;
-    POG_TRY(global_relabel(g));
-    POG_TRY(count_active(g, active));
+    if (!(g->flags & POG_FLAG_NO_PREPUSH)) {
+        POG_TRY_CUDA(pog::launch_column_prepush(g->grid, g->stream));
+        g->stats[ST_LAUNCHES] += 1;
+    }
+    POG_TRY(global_relabel(g, active));
     g->stats[ST_ROUNDS] = 1;
     g->stats[ST_ACTIVE0] = active;
     const bool gap = !(g->flags & POG_FLAG_NO_GAP);
@@ -154,7 +138,9 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
     while (active > 0) {
         if (g->stats[ST_ROUNDS] >= g->max_rounds) return POG_E_NOCONVERGE;
         for (int k = 0; k < g->sweeps_per_relabel; ++k) {
-            POG_TRY_CUDA(timed(g, TM_SWEEP, [&] { return pog::launch_sweep(g->grid, g->tile_sweeps, g->stream); }));
+            POG_TRY_CUDA(timed(g, TM_SWEEP, [&] {
+                return pog::launch_sweep(g->grid, g->queue_a, &g->bfs_sync->size[0], g->tile_sweeps, g->stream);
+            }));
             if (gap && k + 1 == half) {
                 POG_TRY(reset_field(g, &DevCounters::raised));
                 POG_TRY(reset_field(g, &DevCounters::max_label));
@@ -164,21 +150,20 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
             }
         }
         g->stats[ST_SWEEP] += g->sweeps_per_relabel;
-        g->stats[ST_LAUNCHES] += g->sweeps_per_relabel;
-        POG_TRY(global_relabel(g));
-        POG_TRY(count_active(g, active));
+        g->stats[ST_LAUNCHES] += 2 * g->sweeps_per_relabel;
+        POG_TRY(global_relabel(g, active));
         g->stats[ST_ROUNDS]++;
     }
     // Maximum preflow reached: extract the minimal cut, the heights and the flow value.
-    POG_TRY_CUDA(pog::launch_cut_init(g->grid, g->stream));
-    g->stats[ST_LAUNCHES] += 4;  // cut init, heights, excess sum, and the build's two kernels - 1
-    POG_TRY(relax_to_fixpoint(
-        g, [&] { return timed(g, TM_CUT, [&] { return pog::launch_cut_relax(g->grid, g->stream); }); },
-        g->stats[ST_CUT]));
+    POG_TRY_CUDA(timed(g, TM_CUT, [&] {
+        return pog::launch_cut_reach(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
+    }));
+    g->stats[ST_LAUNCHES] += 5;  // cut, heights, excess sum, and the build's two kernels
     POG_TRY_CUDA(pog::launch_heights(g->grid, g->heights, g->stream));
     POG_TRY(reset_field(g, &DevCounters::excess_sum));
     POG_TRY_CUDA(pog::launch_excess_sum(g->grid, g->stream));
     POG_TRY(read_counters(g));
+    g->stats[ST_CUT] = g->ctr_host->max_label;  // BFS levels of the cut extraction
     const DevCounters &c = *g->ctr_host;
     g->flow = (long long)c.bottom_const + (long long)c.src_total - (long long)c.excess_sum;
     fold_timers(g);
@@ -207,7 +192,9 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
     const size_t per = align_up((size_t)N * sizeof(int32_t), 256);
     const size_t heights = align_up((size_t)X * Y * sizeof(int32_t), 256);
     const size_t ctr = align_up(sizeof(DevCounters), 256) + (size_t)kGapLevels / 8;
-    g->arena_bytes = per * arrays + heights + ctr;
+    const size_t sync = align_up(sizeof(pog::BfsSync), 256);
+    const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
+    g->arena_bytes = per * (arrays + 2) + heights + ctr + sync + trace;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -234,8 +221,17 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
         *slots[i] = i < arrays ? reinterpret_cast<int32_t *>(p) : nullptr;
         if (i < arrays) p += per;
     }
+    g->queue_a = reinterpret_cast<int32_t *>(p);
+    p += per;
+    g->queue_b = reinterpret_cast<int32_t *>(p);
+    p += per;
     g->heights = reinterpret_cast<int32_t *>(p);
     p += heights;
+    g->bfs_sync = reinterpret_cast<pog::BfsSync *>(p);
+    p += sync;
+    g->trace = reinterpret_cast<pog::LevelTrace *>(p);
+    p += trace;
+    gr.trace = g->trace;
     g->ctr = reinterpret_cast<DevCounters *>(p);
     gr.ctr = g->ctr;
     e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
@@ -350,6 +346,32 @@ pog_status pog_export_state(const pog_graph *g, int32_t *excess, int32_t *sink, 
         if (copies[i].dst)
             POG_TRY_CUDA(cudaMemcpyAsync(copies[i].dst, copies[i].src, bytes, cudaMemcpyDeviceToHost, g->stream));
     POG_TRY_CUDA(cudaStreamSynchronize(g->stream));
+    return POG_OK;
+}
+
+pog_status pog_trace(const pog_graph *g, int64_t *out, int32_t max_levels, int32_t *levels_out) {
+    if (!g || !out || max_levels < 0 || !levels_out) return POG_E_INVALID;
+    const int n = max_levels < pog::kTraceLevels ? max_levels : pog::kTraceLevels;
+    pog::LevelTrace *tmp = static_cast<pog::LevelTrace *>(std::malloc(sizeof(pog::LevelTrace) * (n ? n : 1)));
+    if (!tmp) return POG_E_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(tmp, g->trace, sizeof(pog::LevelTrace) * n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        std::free(tmp);
+        return from_cuda(e);
+    }
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+        out[3 * i] = tmp[i].size;
+        out[3 * i + 1] = tmp[i].mode;
+        out[3 * i + 2] = tmp[i].t_ns;
+        if (tmp[i].mode == -1) {
+            used = i + 1;
+            break;
+        }
+    }
+    *levels_out = used;
+    std::free(tmp);
     return POG_OK;
 }
 

@@ -1,0 +1,250 @@
+// Level-synchronous frontier BFS on the implicit residual graph, one cooperative launch
+// per search: every level expands the current frontier queue into the next one, and the
+// blocks meet at a grid barrier between levels (Section 3.2.2: the software barrier per
+// level of the level-synchronised global relabel; Algorithm 3).
+//
+//   global relabel (reverse BFS from t): labels = exact residual distance to the sink,
+//     INF where t is unreachable (which subsumes the gap heuristic at relabel time);
+//     fused with the termination count of active nodes (Section 3.2.4).
+//   cut extraction (forward BFS): marks = nodes reachable in the residual graph from the
+//     nodes that hold excess, i.e. the source side of the minimal minimum cut.
+//
+// Frontier appends are warp-aggregated; a node joins a frontier once, through an
+// atomicCAS on its label. The grid barrier spins with an iteration limit; on timeout it
+// raises POG_ERR_TIMEOUT and every block leaves.
+#include <cooperative_groups.h>
+
+#include "pog_internal.cuh"
+#include "pog_launch.h"
+
+namespace pog {
+
+namespace {
+
+constexpr int kBfsThreads = 256;
+constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1-2 s of polling at worst
+constexpr int kBottomUpRatio = 8;  // bottom-up once the frontier exceeds 1/8 of the unlabelled nodes
+
+// Sense-reversing grid barrier over co-resident blocks; false once the wait timed out.
+__device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *gen = &s->gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(&s->count, 1u) == nblocks - 1) {
+            s->count = 0;
+            __threadfence();
+            atomicAdd(&s->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > kBarrierSpinLimit || (*(volatile int *)err & POG_ERR_TIMEOUT)) {
+                    atomicOr(err, POG_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok;
+}
+
+// Append `u` to a queue; the lanes that append together share one atomic.
+__device__ __forceinline__ void warp_append(int u, int *queue, int *size) {
+    namespace cg = cooperative_groups;
+    const cg::coalesced_group grp = cg::coalesced_threads();
+    int base = 0;
+    if (grp.thread_rank() == 0) base = atomicAdd(size, (int)grp.size());
+    base = grp.shfl(base, 0);
+    queue[base + grp.thread_rank()] = u;
+}
+
+__device__ __forceinline__ void decode(const Grid &g, int u, int &x, int &y, int &z) {
+    z = u % g.Z;
+    const int col = u / g.Z;
+    x = col / g.Y;
+    y = col - x * g.Y;
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa, int *qb, BfsSync *sync) {
+    const unsigned nblocks = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    int *err = &g.ctr->error;
+    BfsSync *s = sync;
+    // level 1: nodes whose sink arc is residual; everything else starts unreachable
+    for (int base = blockIdx.x * blockDim.x; base < g.N; base += stride) {
+        const int u = base + threadIdx.x;
+        if (u < g.N) {
+            const bool first = (u % g.Z != 0) && g.snk[u] > 0;
+            g.lab[u] = first ? 1 : POG_INF;
+            if (first) warp_append(u, qa, &s->size[1]);
+        }
+    }
+    if (!grid_sync(s, nblocks, err)) return;
+    int level = 1;
+    int *cur = qa, *nxt = qb;
+    long long unvisited = (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
+    __shared__ int frontier;
+    for (;;) {
+        if (threadIdx.x == 0) frontier = *(volatile int *)&s->size[level % 3];
+        __syncthreads();
+        const int n = frontier;
+        __syncthreads();
+        if (n == 0) break;
+        unvisited -= n;
+        const bool bottom_up = (long long)n * kBottomUpRatio > unvisited;
+        if (tid == 0) {
+            s->size[(level + 2) % 3] = 0;  // level-1's counter, free again
+            if (g.trace && level <= kTraceLevels) {
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                g.trace[level - 1] = LevelTrace{n, bottom_up ? 1 : 0, (long long)t, 0};
+            }
+        }
+        if (bottom_up) {
+            // bottom-up: every unlabelled node looks for a residual arc into this level;
+            // neighbours sit at a fixed offset across a warp, so every load is coalesced
+            for (int u = tid; u < g.N; u += stride) {
+                if (ldcg(g.lab + u) != POG_INF) continue;
+                int x, y, z;
+                decode(g, u, x, y, z);
+                if (z == 0) continue;
+                Hood hd;
+                gather_out<SOFT>(g, u, x, y, z, hd);
+                bool hit = false;
+#pragma unroll
+                for (int k = 0; k < kMaxArcs; ++k) hit |= hd.lab[k] == level;
+                if (hit) {
+                    g.lab[u] = level + 1;
+                    warp_append(u, nxt, &s->size[(level + 1) % 3]);
+                }
+            }
+        } else {
+            // top-down: expand the frontier queue along residual arcs into its nodes
+            for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+                const int i = base + threadIdx.x;
+                if (i < n) {
+                    const int v = cur[i];
+                    int x, y, z;
+                    decode(g, v, x, y, z);
+                    Hood hd;
+                    gather_in<SOFT>(g, v, x, y, z, hd);
+#pragma unroll
+                    for (int k = 0; k < kMaxArcs; ++k)
+                        if (hd.res[k] > 0 && hd.lab[k] == POG_INF &&
+                            atomicCAS(g.lab + hd.node[k], POG_INF, level + 1) == POG_INF)
+                            warp_append(hd.node[k], nxt, &s->size[(level + 1) % 3]);
+                }
+            }
+        }
+        if (!grid_sync(s, nblocks, err)) return;
+        int *t = cur;
+        cur = nxt;
+        nxt = t;
+        ++level;
+    }
+    if (tid == 0 && g.trace && level <= kTraceLevels) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        g.trace[level - 1] = LevelTrace{0, -1, (long long)t, 0};
+    }
+    // termination test: active nodes (excess > 0 and a finite label)
+    unsigned long long active = 0;
+    for (int u = tid; u < g.N; u += stride)
+        if (u % g.Z != 0 && g.exc[u] > 0 && g.lab[u] < POG_INF) ++active;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(0xffffffffu, active, o);
+    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&g.ctr->active, active);
+    if (tid == 0) g.ctr->max_label = level;
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kBfsThreads) k_cut_reach(Grid g, int *qa, int *qb, BfsSync *sync) {
+    const unsigned nblocks = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    int *err = &g.ctr->error;
+    BfsSync *s = sync;
+    for (int base = blockIdx.x * blockDim.x; base < g.N; base += stride) {
+        const int u = base + threadIdx.x;
+        if (u < g.N) {
+            const bool seed = (u % g.Z != 0) && g.exc[u] > 0;
+            g.lab[u] = seed ? 1 : 0;
+            if (seed) warp_append(u, qa, &s->size[1]);
+        }
+    }
+    if (!grid_sync(s, nblocks, err)) return;
+    int level = 1;
+    int *cur = qa, *nxt = qb;
+    __shared__ int frontier;
+    for (;;) {
+        if (threadIdx.x == 0) frontier = *(volatile int *)&s->size[level % 3];
+        __syncthreads();
+        const int n = frontier;
+        __syncthreads();
+        if (n == 0) break;
+        if (tid == 0) s->size[(level + 2) % 3] = 0;
+        for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+            const int i = base + threadIdx.x;
+            if (i < n) {
+                const int u = cur[i];
+                int x, y, z;
+                decode(g, u, x, y, z);
+                Hood hd;
+                gather_out<SOFT>(g, u, x, y, z, hd);
+#pragma unroll
+                for (int k = 0; k < kMaxArcs; ++k)
+                    if (hd.res[k] > 0 && hd.lab[k] == 0 && atomicCAS(g.lab + hd.node[k], 0, 1) == 0)
+                        warp_append(hd.node[k], nxt, &s->size[(level + 1) % 3]);
+            }
+        }
+        if (!grid_sync(s, nblocks, err)) return;
+        int *t = cur;
+        cur = nxt;
+        nxt = t;
+        ++level;
+    }
+    if (tid == 0) g.ctr->max_label = level;
+}
+
+template <class K>
+cudaError_t coop_launch(K kernel, const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+                        cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+    if (!coop) return cudaErrorNotSupported;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBfsThreads, 0)) != cudaSuccess) return e;
+    const int want = blocks_per_sm > 0 ? blocks_per_sm : 2;
+    const int blocks = sms * (per_sm < want ? per_sm : want);  // co-resident by construction
+    if (blocks < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaMemsetAsync(sync, 0, sizeof(BfsSync), st)) != cudaSuccess) return e;
+    Grid gg = g;
+    void *args[] = {&gg, &qa, &qb, &sync};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(kernel), blocks, kBfsThreads, args, 0, st);
+}
+
+}  // namespace
+
+cudaError_t launch_global_relabel(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+                                  cudaStream_t st) {
+    if (g.gs[0]) return coop_launch(k_global_relabel<true>, g, qa, qb, sync, blocks_per_sm, st);
+    return coop_launch(k_global_relabel<false>, g, qa, qb, sync, blocks_per_sm, st);
+}
+
+cudaError_t launch_cut_reach(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
+    if (g.gs[0]) return coop_launch(k_cut_reach<true>, g, qa, qb, sync, blocks_per_sm, st);
+    return coop_launch(k_cut_reach<false>, g, qa, qb, sync, blocks_per_sm, st);
+}
+
+}  // namespace pog

@@ -26,6 +26,7 @@
 
 #define POG_ERR_COST_RANGE 1     // |c| >= 2^30 or a non-finite float cost
 #define POG_ERR_FLOW_RANGE 2     // an infinite arc's flow or an excess reached int32 range
+#define POG_ERR_TIMEOUT 4        // a bounded grid-barrier wait gave up
 
 namespace pog {
 
@@ -46,6 +47,21 @@ struct DevCounters {
     int pad[4];
 };
 
+// Grid-barrier and frontier-size words of a cooperative BFS launch.
+struct BfsSync {
+    unsigned count;  // blocks arrived at the current barrier
+    unsigned gen;    // barrier generation
+    int size[3];     // frontier sizes, indexed by level mod 3
+    int pad[3];
+};
+
+// Per-level trace of the last global relabel: frontier size, mode (0 top-down, 1
+// bottom-up) and the device clock (ns) when the level started.
+constexpr int kTraceLevels = 4096;
+struct LevelTrace {
+    long long size, mode, t_ns, pad;
+};
+
 struct Grid {
     int X, Y, Z, delta, alpha;
     int N;                 // X*Y*Z
@@ -56,6 +72,7 @@ struct Grid {
     int32_t *fh[4];        // flow on the hard arcs, per direction
     int32_t *gs[2];        // net soft flow towards x+1 / y+1
     DevCounters *ctr;
+    LevelTrace *trace;     // per-level trace of the global relabel (may be null)
 };
 
 enum ArcKind : int { ARC_NONE = -1, ARC_SINK = 0, ARC_DOWN, ARC_UP, ARC_HOUT, ARC_HIN, ARC_SOFT };
@@ -72,17 +89,32 @@ __device__ __forceinline__ int nb_offset(const Grid &g, int x, int y, int d, boo
     }
 }
 
-// Visit every residual arc u -> v of a non-bottom node u (the sink arc excluded):
-// f(kind, d, v, residual). Residuals are read with L2-coherent loads.
-template <bool SOFT, class F>
-__device__ __forceinline__ void for_each_residual_arc(const Grid &g, int u, int x, int y, int z, F &&f) {
+// Gathered neighbourhood of a node: up to 14 arcs (2 vertical, 3 per direction) with
+// their residual capacity and the far end's label, all loaded before any decision so
+// the loads overlap instead of forming a dependent chain.
+constexpr int kMaxArcs = 14;
+
+struct Hood {
+    int node[kMaxArcs];
+    int res[kMaxArcs];   // residual capacity, 0 for an absent arc
+    int lab[kMaxArcs];   // label (or mark) of the far end, POG_INF for an absent arc
+};
+
+// Out-arcs of u: slot 0 down, 1 up, 2+3d hard out, 3+3d hard in (reverse), 4+3d soft.
+template <bool SOFT>
+__device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, int z, Hood &h) {
+#pragma unroll
+    for (int i = 0; i < kMaxArcs; ++i) {
+        h.res[i] = 0;
+        h.node[i] = u;
+    }
     if (z >= 2) {
-        const int r = POG_CAP_INF - ldcg(g.fdn + u);
-        if (r > 0) f(ARC_DOWN, 0, u - 1, r);
+        h.node[0] = u - 1;
+        h.res[0] = POG_CAP_INF - ldcg(g.fdn + u);
     }
     if (z + 1 < g.Z) {
-        const int r = ldcg(g.fdn + u + 1);
-        if (r > 0) f(ARC_UP, 0, u + 1, r);
+        h.node[1] = u + 1;
+        h.res[1] = ldcg(g.fdn + u + 1);
     }
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
@@ -90,21 +122,63 @@ __device__ __forceinline__ void for_each_residual_arc(const Grid &g, int u, int 
         const int off = nb_offset(g, x, y, d, ok);
         if (!ok) continue;
         if (z - g.delta >= 1) {
-            const int r = POG_CAP_INF - ldcg(g.fh[d] + u);
-            if (r > 0) f(ARC_HOUT, d, u + off - g.delta, r);
+            h.node[2 + 3 * d] = u + off - g.delta;
+            h.res[2 + 3 * d] = POG_CAP_INF - ldcg(g.fh[d] + u);
         }
         if (z + g.delta < g.Z) {
             const int v = u + off + g.delta;
-            const int r = ldcg(g.fh[d ^ 1] + v);
-            if (r > 0) f(ARC_HIN, d, v, r);
+            h.node[3 + 3 * d] = v;
+            h.res[3 + 3 * d] = ldcg(g.fh[d ^ 1] + v);
         }
         if (SOFT) {
             const int v = u + off;
-            // d odd: towards x+1 / y+1, the pair lives at u; d even: it lives at v.
-            const int r = (d & 1) ? g.alpha - ldcg(g.gs[d >> 1] + u) : g.alpha + ldcg(g.gs[d >> 1] + v);
-            if (r > 0) f(ARC_SOFT, d, v, r);
+            h.node[4 + 3 * d] = v;
+            h.res[4 + 3 * d] = (d & 1) ? g.alpha - ldcg(g.gs[d >> 1] + u) : g.alpha + ldcg(g.gs[d >> 1] + v);
         }
     }
+#pragma unroll
+    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = h.res[i] > 0 ? ldcg(g.lab + h.node[i]) : POG_INF;
+}
+
+// In-arcs of v (arcs u -> v): slot 0 from above, 1 from below, 2+3d hard arc of
+// (q, z+D), 3+3d reverse of v's hard arc, 4+3d soft.
+template <bool SOFT>
+__device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, int z, Hood &h) {
+#pragma unroll
+    for (int i = 0; i < kMaxArcs; ++i) {
+        h.res[i] = 0;
+        h.node[i] = v;
+    }
+    if (z + 1 < g.Z) {
+        h.node[0] = v + 1;
+        h.res[0] = POG_CAP_INF - ldcg(g.fdn + v + 1);
+    }
+    if (z >= 2) {
+        h.node[1] = v - 1;
+        h.res[1] = ldcg(g.fdn + v);
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        bool ok;
+        const int off = nb_offset(g, x, y, d, ok);
+        if (!ok) continue;
+        if (z + g.delta < g.Z) {
+            const int u = v + off + g.delta;
+            h.node[2 + 3 * d] = u;
+            h.res[2 + 3 * d] = POG_CAP_INF - ldcg(g.fh[d ^ 1] + u);
+        }
+        if (z - g.delta >= 1) {
+            h.node[3 + 3 * d] = v + off - g.delta;
+            h.res[3 + 3 * d] = ldcg(g.fh[d] + v);
+        }
+        if (SOFT) {
+            const int u = v + off;
+            h.node[4 + 3 * d] = u;
+            h.res[4 + 3 * d] = (d & 1) ? g.alpha + ldcg(g.gs[d >> 1] + v) : g.alpha - ldcg(g.gs[d >> 1] + u);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = h.res[i] > 0 ? ldcg(g.lab + h.node[i]) : POG_INF;
 }
 
 }  // namespace pog
@@ -118,11 +192,14 @@ struct pog_graph {
     size_t arena_bytes;
     pog::Grid grid;
     int32_t *heights;            // device [X*Y]
+    int32_t *queue_a, *queue_b;  // device [N] each: BFS frontiers
+    pog::BfsSync *bfs_sync;      // device: grid barrier + frontier sizes
+    pog::LevelTrace *trace;      // device [kTraceLevels]: last global relabel
     pog::DevCounters *ctr;       // device
     pog::DevCounters *ctr_host;  // pinned host mirror
     int solved;
     long long flow;
-    int sweeps_per_relabel, max_rounds, tile_sweeps, flags;
+    int sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks;
     long long stats[8];
     // POG_FLAG_TIMING: event pairs per kernel family, folded into ms[] after a sync
     struct Timer {

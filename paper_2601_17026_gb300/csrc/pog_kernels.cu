@@ -1,6 +1,8 @@
 // Node-parallel kernels of the GB300 min-cut solver: graph construction, push/relabel
 // sweeps, global relabelling by reverse BFS, gap relabelling, termination counts, cut
 // extraction, surface heights, quantisation and the energy backward.
+#include <cooperative_groups.h>
+
 #include "pog_internal.cuh"
 #include "pog_launch.h"
 
@@ -117,16 +119,74 @@ __global__ void k_bottom_const(Grid g, Cost cost) {
 }
 
 // ----------------------------------------------------------------------------------
+// Column pre-push: before the first global relabel, every column pushes its excess down
+// its infinite down arcs (Section 1.2: (x,y,z) -> (x,y,z-1)), absorbing it into the sink
+// arcs it passes. Scanning from the top, the flow leaving node z downwards is
+//   c_z = max(0, c_{z+1} + e_z - s_z),
+// a composition of maps c -> max(b, c + a) that a warp evaluates as a prefix scan over 32
+// heights at a time. What reaches z = 1 stays there as excess. Only pushes along
+// residual arcs are made, so the result is a preflow; it is the starting point of
+// push-relabel (the paper starts from the saturated source arcs alone).
+// ----------------------------------------------------------------------------------
+
+__global__ void k_column_prepush(Grid g) {
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (col >= g.X * g.Y) return;
+    const long long base = (long long)col * g.Z;
+    long long carry = 0;  // flow entering the current chunk from above
+    bool overflow = false;
+    for (int zhi = g.Z - 1; zhi >= 1; zhi -= 32) {
+        const int z = zhi - lane;  // lane 0 is the top of the chunk
+        const bool valid = z >= 1;
+        const long long e = valid ? g.exc[base + z] : 0;
+        const long long sk = valid ? g.snk[base + z] : 0;
+        long long a = e - sk, b = 0;  // this node's map c -> max(b, c + a)
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {  // compose with the maps of the nodes above
+            const long long pa = __shfl_up_sync(0xffffffffu, a, off);
+            const long long pb = __shfl_up_sync(0xffffffffu, b, off);
+            if (lane >= off) {
+                b = max(b, pb + a);
+                a = pa + a;
+            }
+        }
+        const long long c_out = max(b, carry + a);
+        long long c_in = __shfl_up_sync(0xffffffffu, c_out, 1);
+        if (lane == 0) c_in = carry;
+        if (valid) {
+            const long long absorbed = c_in + e - c_out;  // into the sink arc
+            g.snk[base + z] = (int)(sk - absorbed);
+            if (z >= 2) {
+                g.fdn[base + z] = (int)c_out;
+                g.exc[base + z] = 0;
+            } else {
+                g.exc[base + z] = (int)c_out;
+            }
+            if (c_out > 0x7fffffffll) overflow = true;
+        }
+        carry = __shfl_sync(0xffffffffu, c_out, 31);
+    }
+    if (overflow) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
+}
+
+// ----------------------------------------------------------------------------------
 // Push/relabel sweep (Section 2.1, Algorithm 2), lock-free: each node is discharged
 // only by its own thread; neighbours' excess and the paired arc values are changed
 // with atomics. Every value a thread reads can only move, concurrently, in the
 // direction that makes its push smaller than allowed, so stale reads are safe.
 // ----------------------------------------------------------------------------------
 
+// Arc kind of a gathered slot (see gather_out).
+__device__ __forceinline__ int slot_kind(int k) {
+    if (k == 0) return ARC_DOWN;
+    if (k == 1) return ARC_UP;
+    const int r = (k - 2) % 3;
+    return r == 0 ? ARC_HOUT : (r == 1 ? ARC_HIN : ARC_SOFT);
+}
+
 template <bool SOFT>
-__global__ void k_push_relabel(Grid g, int ops) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= g.N) return;
+__device__ __forceinline__ void discharge(const Grid &g, int u, int ops) {
     const int z = u % g.Z;
     if (z == 0) return;
     const int col = u / g.Z;
@@ -135,102 +195,80 @@ __global__ void k_push_relabel(Grid g, int ops) {
         const int e = ldcg(g.exc + u);
         const int h = ldcg(g.lab + u);
         if (e <= 0 || h >= POG_INF) return;
-        int best = POG_INF, kind = ARC_NONE, dir = 0, target = -1, res = 0;
         const int s = ldcg(g.snk + u);
-        if (s > 0) {
-            best = 0;
-            kind = ARC_SINK;
-            res = s;
-        } else {
-            for_each_residual_arc<SOFT>(g, u, x, y, z, [&](int k, int d, int v, int r) {
-                const int l = ldcg(g.lab + v);
-                if (l < best) {
-                    best = l;
-                    kind = k;
-                    dir = d;
-                    target = v;
-                    res = r;
-                }
-            });
-        }
-        if (kind != ARC_NONE && h > best) {
-            const int delta = e < res ? e : res;
-            int sat = 0;
-            switch (kind) {
-                case ARC_SINK: g.snk[u] = s - delta; break;
-                case ARC_DOWN: sat = atomicAdd(g.fdn + u, delta) + delta == POG_CAP_INF; break;
-                case ARC_UP: atomicSub(g.fdn + u + 1, delta); break;
-                case ARC_HOUT: sat = atomicAdd(g.fh[dir] + u, delta) + delta == POG_CAP_INF; break;
-                case ARC_HIN: atomicSub(g.fh[dir ^ 1] + target, delta); break;
-                default:
-                    if (dir & 1) atomicAdd(g.gs[dir >> 1] + u, delta);
-                    else atomicSub(g.gs[dir >> 1] + target, delta);
-                    break;
+        if (s > 0) {  // the sink arc: label 0, always the lowest
+            if (h > 0) {
+                const int delta = e < s ? e : s;
+                g.snk[u] = s - delta;
+                atomicSub(g.exc + u, delta);
+            } else {
+                g.lab[u] = 1;
             }
-            atomicSub(g.exc + u, delta);
-            if (kind != ARC_SINK) {
-                const int old = atomicAdd(g.exc + target, delta);
-                if (old > 0x7fffffff - delta) sat = 1;
-            }
-            if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
-        } else {
-            g.lab[u] = best >= POG_INF - 1 ? POG_INF : best + 1;  // relabel
+            continue;
         }
+        Hood hd;
+        gather_out<SOFT>(g, u, x, y, z, hd);
+        int best = POG_INF, k = -1;
+#pragma unroll
+        for (int i = 0; i < kMaxArcs; ++i)
+            if (hd.lab[i] < best) {
+                best = hd.lab[i];
+                k = i;
+            }
+        if (k < 0 || h <= best) {  // relabel (Algorithm 2): one above the lowest residual neighbour
+            g.lab[u] = best >= POG_INF - 1 ? POG_INF : best + 1;
+            continue;
+        }
+        int res = 0, target = 0;
+#pragma unroll
+        for (int i = 0; i < kMaxArcs; ++i)
+            if (i == k) {
+                res = hd.res[i];
+                target = hd.node[i];
+            }
+        const int delta = e < res ? e : res;
+        const int kind = slot_kind(k);
+        const int dir = k >= 2 ? (k - 2) / 3 : 0;
+        int sat = 0;
+        switch (kind) {
+            case ARC_DOWN: sat = atomicAdd(g.fdn + u, delta) + delta == POG_CAP_INF; break;
+            case ARC_UP: atomicSub(g.fdn + u + 1, delta); break;
+            case ARC_HOUT: sat = atomicAdd(g.fh[dir] + u, delta) + delta == POG_CAP_INF; break;
+            case ARC_HIN: atomicSub(g.fh[dir ^ 1] + target, delta); break;
+            default:
+                if (dir & 1) atomicAdd(g.gs[dir >> 1] + u, delta);
+                else atomicSub(g.gs[dir >> 1] + target, delta);
+                break;
+        }
+        atomicSub(g.exc + u, delta);
+        const int old = atomicAdd(g.exc + target, delta);
+        if (old > 0x7fffffff - delta) sat = 1;
+        if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
     }
 }
 
-// ----------------------------------------------------------------------------------
-// Global relabelling (Section 3.2.2, Algorithm 3): exact distances to the sink in the
-// residual graph. Level 1 holds the nodes whose sink arc is residual. A relaxation
-// pass lowers d(u) to min over residual arcs (u, v) of d(v) + 1; labels only decrease
-// and each is the length of a real path, so the fixpoint is the BFS distance; nodes
-// that never get a finite value cannot reach t (the gap effect, Section 2.1).
-// ----------------------------------------------------------------------------------
-
-__global__ void k_bfs_init(Grid g) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= g.N) return;
-    const int z = u % g.Z;
-    g.lab[u] = (z != 0 && g.snk[u] > 0) ? 1 : POG_INF;
+// A sweep is two launches: the active nodes (excess > 0, finite label) are compacted
+// into a list by a coalesced scan, then one thread per listed node discharges it with
+// up to `ops` push or relabel operations. Clustered active nodes thus spread over all
+// threads instead of serialising on the few that own their region.
+__global__ void __launch_bounds__(kThreads) k_collect_active(Grid g, int *list, int *count) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
+        if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
+        namespace cg = cooperative_groups;
+        const cg::coalesced_group grp = cg::coalesced_threads();
+        int base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(count, (int)grp.size());
+        base = grp.shfl(base, 0);
+        list[base + grp.thread_rank()] = u;
+    }
 }
 
 template <bool SOFT>
-__global__ void k_bfs_relax(Grid g) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= g.N) return;
-    const int z = u % g.Z;
-    if (z == 0) return;
-    const int h = ldcg(g.lab + u);
-    if (h <= 1) return;
-    const int col = u / g.Z;
-    const int x = col / g.Y, y = col - x * g.Y;
-    int best = h;
-    for_each_residual_arc<SOFT>(g, u, x, y, z, [&](int, int, int v, int) {
-        const int l = ldcg(g.lab + v) + 1;
-        if (l < best) best = l;
-    });
-    if (best < h) {
-        g.lab[u] = best;
-        g.ctr->changed = 1;
-    }
-}
-
-// Active nodes (excess > 0, finite label) and the largest finite label.
-__global__ void k_count_active(Grid g) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long a = 0;
-    int lmax = 0;
-    if (u < g.N && u % g.Z != 0) {
-        const int l = g.lab[u];
-        if (l < POG_INF) {
-            lmax = l;
-            if (g.exc[u] > 0) a = 1;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
-    if ((threadIdx.x & 31) == 0 && lmax > 0) atomicMax(&g.ctr->max_label, lmax);
-    block_add_u64(a, &g.ctr->active);
+__global__ void __launch_bounds__(kThreads) k_push_relabel(Grid g, const int *list, const int *count, int ops) {
+    const int n = *count;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) discharge<SOFT>(g, list[i], ops);
 }
 
 // ----------------------------------------------------------------------------------
@@ -238,17 +276,26 @@ __global__ void k_count_active(Grid g) {
 // those cannot reach t and are raised to INF. Level occupancy is a bitmap.
 // ----------------------------------------------------------------------------------
 
+constexpr int kGapSharedWords = 256;  // levels below 8192 are gathered per block first
+
 __global__ void k_gap_occupancy(Grid g, unsigned int *bits, int levels) {
+    __shared__ unsigned int local[kGapSharedWords];
+    for (int i = threadIdx.x; i < kGapSharedWords; i += blockDim.x) local[i] = 0u;
+    __syncthreads();
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     int lmax = 0;
     if (u < g.N && u % g.Z != 0) {
         const int l = g.lab[u];
-        if (l < levels) atomicOr(bits + (l >> 5), 1u << (l & 31));
+        if (l < kGapSharedWords * 32) atomicOr(local + (l >> 5), 1u << (l & 31));
+        else if (l < levels) atomicOr(bits + (l >> 5), 1u << (l & 31));
         if (l < POG_INF) lmax = l;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
     if ((threadIdx.x & 31) == 0 && lmax > 0) atomicMax(&g.ctr->max_label, lmax);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kGapSharedWords; i += blockDim.x)
+        if (local[i]) atomicOr(bits + i, local[i]);
 }
 
 // One block: the first empty level above 0 that lies below the largest finite label.
@@ -281,36 +328,6 @@ __global__ void k_gap_raise(Grid g) {
         }
     }
     block_add_u64(r, &g.ctr->raised);
-}
-
-// ----------------------------------------------------------------------------------
-// Cut extraction: the source side of the minimal minimum cut is the set of nodes
-// reachable in the residual graph from s and from every node with excess (the bottom
-// layer is part of s and has no residual arc out). Marks live in the label array.
-// ----------------------------------------------------------------------------------
-
-__global__ void k_cut_init(Grid g) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= g.N) return;
-    g.lab[u] = (u % g.Z != 0 && g.exc[u] > 0) ? 1 : 0;
-}
-
-template <bool SOFT>
-__global__ void k_cut_relax(Grid g) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= g.N) return;
-    const int z = u % g.Z;
-    if (z == 0 || ldcg(g.lab + u) == 0) return;
-    const int col = u / g.Z;
-    const int x = col / g.Y, y = col - x * g.Y;
-    bool any = false;
-    for_each_residual_arc<SOFT>(g, u, x, y, z, [&](int, int, int v, int) {
-        if (ldcg(g.lab + v) == 0) {
-            g.lab[v] = 1;
-            any = true;
-        }
-    });
-    if (any) g.ctr->changed = 1;
 }
 
 // One warp per column: the top marked node (0 when only the bottom layer is in S).
@@ -436,19 +453,32 @@ cudaError_t launch_build_f32(const Grid &g, const float *cost, float scale, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const Grid &g, int ops, cudaStream_t st) {
-    if (g.gs[0]) POG_LAUNCH(k_push_relabel<true>, g.N, st, g, ops);
-    POG_LAUNCH(k_push_relabel<false>, g.N, st, g, ops);
+cudaError_t launch_column_prepush(const Grid &g, cudaStream_t st) {
+    const long long threads = (long long)g.X * g.Y * 32;
+    POG_LAUNCH(k_column_prepush, threads, st, g);
 }
 
-cudaError_t launch_bfs_init(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_bfs_init, g.N, st, g); }
-
-cudaError_t launch_bfs_relax(const Grid &g, cudaStream_t st) {
-    if (g.gs[0]) POG_LAUNCH(k_bfs_relax<true>, g.N, st, g);
-    POG_LAUNCH(k_bfs_relax<false>, g.N, st, g);
+int sweep_blocks(const Grid &g) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 148;
+    }
+    const long long need = blocks_for(g.N);
+    const long long cap = (long long)sms * 8;
+    return (int)(need < cap ? need : cap);
 }
 
-cudaError_t launch_count_active(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_count_active, g.N, st, g); }
+cudaError_t launch_sweep(const Grid &g, int *list, int *count, int ops, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int blocks = sweep_blocks(g);
+    k_collect_active<<<blocks, kThreads, 0, st>>>(g, list, count);
+    if (g.gs[0]) k_push_relabel<true><<<blocks, kThreads, 0, st>>>(g, list, count, ops);
+    else k_push_relabel<false><<<blocks, kThreads, 0, st>>>(g, list, count, ops);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gap(const Grid &g, unsigned int *bits, int levels, cudaStream_t st) {
     cudaMemsetAsync(bits, 0, (size_t)(levels / 32) * sizeof(unsigned int), st);
@@ -456,13 +486,6 @@ cudaError_t launch_gap(const Grid &g, unsigned int *bits, int levels, cudaStream
     k_gap_find<<<1, 1024, 0, st>>>(g, bits, levels);
     k_gap_raise<<<blocks_for(g.N), kThreads, 0, st>>>(g);
     return cudaGetLastError();
-}
-
-cudaError_t launch_cut_init(const Grid &g, cudaStream_t st) { POG_LAUNCH(k_cut_init, g.N, st, g); }
-
-cudaError_t launch_cut_relax(const Grid &g, cudaStream_t st) {
-    if (g.gs[0]) POG_LAUNCH(k_cut_relax<true>, g.N, st, g);
-    POG_LAUNCH(k_cut_relax<false>, g.N, st, g);
 }
 
 cudaError_t launch_heights(const Grid &g, int32_t *heights, cudaStream_t st) {

@@ -7,22 +7,22 @@
 namespace pog {
 
 struct Grid;
+struct BfsSync;
 
 cudaError_t launch_build_i32(const Grid &g, const int32_t *cost, cudaStream_t st);
 cudaError_t launch_build_f32(const Grid &g, const float *cost, float scale, const int32_t *h_aug, int margin,
                              cudaStream_t st);
-cudaError_t launch_sweep(const Grid &g, int ops, cudaStream_t st);
-cudaError_t launch_bfs_init(const Grid &g, cudaStream_t st);
-cudaError_t launch_bfs_relax(const Grid &g, cudaStream_t st);
-cudaError_t launch_count_active(const Grid &g, cudaStream_t st);
+cudaError_t launch_column_prepush(const Grid &g, cudaStream_t st);
+cudaError_t launch_sweep(const Grid &g, int *list, int *count, int ops, cudaStream_t st);
 cudaError_t launch_gap(const Grid &g, unsigned int *bits, int levels, cudaStream_t st);
-cudaError_t launch_cut_init(const Grid &g, cudaStream_t st);
-cudaError_t launch_cut_relax(const Grid &g, cudaStream_t st);
 cudaError_t launch_heights(const Grid &g, int32_t *heights, cudaStream_t st);
 cudaError_t launch_excess_sum(const Grid &g, cudaStream_t st);
 cudaError_t launch_quantise(const float *in, int32_t *out, long long n, float scale, int *err, cudaStream_t st);
 cudaError_t launch_backward(float *grad, const int32_t *h, const int32_t *ht, const int32_t *hh, const float *ge,
                             const float *gh, int B, int XY, int Z, cudaStream_t st);
+cudaError_t launch_global_relabel(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+                                  cudaStream_t st);
+cudaError_t launch_cut_reach(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_surface_energy(const float *cost, float scale, const int32_t *h, int B, int X, int Y, int Z,
                                   int alpha, long long *out, cudaStream_t st);
 

@@ -26,9 +26,10 @@ POG_E_TIMEOUT = 6
 POG_E_STATE = 7
 POG_FLAG_NO_GAP = 1
 POG_FLAG_TIMING = 2
+POG_FLAG_NO_PREPUSH = 4
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
-            "pog_stats", "pog_export_state", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
+            "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
             "pog_surface_energy", "pog_solve_batch"]
 
 
@@ -40,7 +41,8 @@ class PogError(RuntimeError):
 
 class pog_options(ctypes.Structure):
     _fields_ = [("sweeps_per_relabel", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
-                ("tile_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("tile_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32), ("bfs_blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class pog_stats_t(ctypes.Structure):
@@ -80,6 +82,7 @@ def load(path: str = LIB_PATH):
             "pog_surface": [vp, vp],
             "pog_stats": [vp, ctypes.POINTER(pog_stats_t)],
             "pog_export_state": [vp, vp, vp, vp, vp, vp, vp],
+            "pog_trace": [vp, vp, i32, ctypes.POINTER(i32)],
             "pog_quantise": [vp, vp, i64, f32, vp],
             "pog_backward": [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp],
             "pog_solve_batch": [i32, ctypes.POINTER(pog_volume), opts, vp, i64p, ctypes.POINTER(vp)],
@@ -119,8 +122,8 @@ def _dev(t, dtype, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_options(sweeps_per_relabel=0, max_rounds=0, tile_sweeps=0, flags=0) -> pog_options:
-    return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags)
+def make_options(sweeps_per_relabel=0, max_rounds=0, tile_sweeps=0, flags=0, bfs_blocks_per_sm=0) -> pog_options:
+    return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks_per_sm)
 
 
 def pog_strerror(status: int) -> str:
@@ -259,6 +262,14 @@ def pog_export_state(g: Graph) -> dict:
     _check(load().pog_export_state(g.handle, p(out["excess"]), p(out["sink"]), p(out["fdown"]), p(out["fhard"]),
                                    p(out["gsoft"]) if g.alpha > 0 else None, p(out["in_cut"])), "pog_export_state")
     return out
+
+
+def pog_trace(g: Graph, max_levels: int = 4096) -> np.ndarray:
+    """int64 [levels, 3]: (frontier size, mode, device ns) per level of the last global relabel."""
+    out = np.zeros(3 * max_levels, dtype=np.int64)
+    n = ctypes.c_int32(0)
+    _check(load().pog_trace(g.handle, ctypes.c_void_p(out.ctypes.data), max_levels, ctypes.byref(n)), "pog_trace")
+    return out[: 3 * n.value].reshape(-1, 3)
 
 
 def pog_free(g: Graph) -> None:
