@@ -106,15 +106,27 @@ def _dist():
     return ws, rank
 
 
-def algorithmic_bytes(N, alpha):
-    """Per-launch algorithmic bytes of each kernel family (see the roofline notes in DESIGN)."""
-    arc_words = 1 + 4 + (2 if alpha > 0 else 0)  # down flow, 4 hard flows, 2 soft pair values
-    S = 4 * (4 + arc_words)  # label, excess, sink residual + arc words
+def algorithmic_bytes(N, alpha, tiles_per_sweep):
+    """Per-launch algorithmic bytes of each kernel family.
+
+    S = residual state per node: label, excess, sink residual (4 B each) plus the arc
+    words (down flow, 4 hard flows, and 2 soft pair values when alpha > 0).
+    tiled sweep: the active-tile scan reads 4 B of excess per node; each visited tile of
+                 1024 nodes is loaded whole (S per node) and its owner-written words
+                 (label, sink residual: 8 B per node) are stored.
+    global relabel: every node's sink residual is read and its label written (8 B), its
+                 arc words read once (4 B each), and the termination count reads
+                 excess and label (8 B).
+    cut: excess read, mark written, arc words read once.
+    build: costs read (4 B per node), state written (S per node).
+    """
+    arc_words = 1 + 4 + (2 if alpha > 0 else 0)
+    S = 4 * (3 + arc_words)
     return {
-        "sweep": 2 * S * N,            # one push/relabel pass over the state: read + write
-        "bfs": (4 + 4 * arc_words) * N + 4 * N,  # labels + arc residuals read, labels written
-        "cut": (4 + 4 * arc_words) * N + 4 * N,
-        "build": 4 * N + S * N,        # costs read, state written
+        "sweep": 4 * N + tiles_per_sweep * 1024 * (S + 8),
+        "bfs": (16 + 4 * arc_words) * N,
+        "cut": (8 + 4 * arc_words) * N,
+        "build": (4 + S) * N,
     }, S
 
 
@@ -202,7 +214,8 @@ def run_ours(args):
     value = ws * N * args.steps / (ms / 1e3) / 1e6
     e2e_value = ws * N * args.steps / (e2e_ms / 1e3) / 1e6
     # roofline of the dominant kernel family, timed live with events on the solve stream
-    bytes_per, S = algorithmic_bytes(N, vol.alpha)
+    tiles_per_sweep = sum(s["tiles_visited"] for s in stats) / max(sum(s["sweeps"] for s in stats), 1)
+    bytes_per, S = algorithmic_bytes(N, vol.alpha, tiles_per_sweep)
     fam = {"sweep": ("sweep_ms", "sweeps"), "bfs": ("bfs_ms", "rounds"), "cut": ("cut_ms", None),
            "build": ("build_ms", None)}
     tot = {k: sum(s[v[0]] for s in stats) for k, v in fam.items()}
@@ -211,7 +224,8 @@ def run_ours(args):
     avg_ms = tot[dom] / max(launches[dom], 1)
     peak, peak_src = _peaks()
     achieved = bytes_per[dom] / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
-    kernel_name = {"sweep": "k_push_relabel", "bfs": "k_bfs_relax", "cut": "k_cut_relax", "build": "k_build"}[dom]
+    kernel_name = {"sweep": "k_tile_push_relabel", "bfs": "k_global_relabel", "cut": "k_cut_reach",
+                   "build": "k_build"}[dom]
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -228,7 +242,8 @@ def run_ours(args):
                      "peak_source": peak_src, "bytes_per_launch": bytes_per[dom],
                      "launches_per_step": launches[dom] / len(stats), "avg_launch_ms": round(avg_ms, 5)},
         "kernel_ms_per_step": {k: round(v / len(stats), 3) for k, v in tot.items()},
-        "solver": {k: st0[k] for k in ("rounds", "sweeps", "bfs_passes", "cut_passes", "gaps", "active_initial")},
+        "solver": {k: st0[k] for k in ("rounds", "sweeps", "bfs_passes", "cut_passes", "gaps", "active_initial",
+                                        "tiles_visited")},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks.summary(),
         "flow": flow,

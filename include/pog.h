@@ -60,7 +60,7 @@ typedef enum {
 typedef struct {
     int32_t sweeps_per_relabel; /* push/relabel sweeps between global relabels (Section 2.1) */
     int32_t max_rounds;         /* cap on global-relabel rounds before POG_E_NOCONVERGE */
-    int32_t tile_sweeps;        /* local sweeps a thread block runs on its shared-memory tile */
+    int32_t tile_sweeps;        /* local push/relabel sweeps per shared-memory tile visit */
     int32_t flags;              /* POG_FLAG_* bits */
     int32_t bfs_blocks_per_sm;  /* resident blocks per SM of the cooperative BFS launches */
     int32_t reserved[3];
@@ -69,6 +69,7 @@ typedef struct {
 #define POG_FLAG_NO_GAP 1     /* disable the gap heuristic between global relabels */
 #define POG_FLAG_TIMING 2     /* time each kernel family with CUDA events on the graph's stream */
 #define POG_FLAG_NO_PREPUSH 4 /* skip the column pre-push along the down arcs */
+#define POG_FLAG_NODE_SWEEPS 8 /* node-parallel sweeps instead of shared-memory tiles */
 
 /* Counters of the last pog_maxflow. */
 typedef struct {
@@ -81,6 +82,7 @@ typedef struct {
     int64_t nodes;           /* X*Y*Z */
     int64_t state_bytes;     /* device bytes of the residual state */
     int64_t launches;        /* kernels launched by pog_build + pog_maxflow */
+    int64_t tiles_visited;   /* tiles staged in shared memory by the tiled sweeps */
     /* device milliseconds per kernel family, with POG_FLAG_TIMING only (else 0) */
     double sweep_ms;         /* push/relabel sweeps */
     double bfs_ms;           /* global-relabel relaxation passes */

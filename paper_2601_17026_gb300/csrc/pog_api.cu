@@ -16,8 +16,11 @@ using pog::Grid;
 namespace {
 
 constexpr int kGapLevels = 1 << 20;          // labels tracked by the gap bitmap
-constexpr int kDefaultSweeps = 16;           // push/relabel sweeps per global relabel
-constexpr int kDefaultOps = 4;               // push/relabel operations per node per sweep
+constexpr int kFirstSweeps = 16;             // sweeps before the first adaptive choice
+constexpr int kMaxSweeps = 1024;             // most sweeps between two global relabels
+constexpr float kRelabelFactor = 1.0f;       // sweep time per round / global relabel time
+constexpr int kNodeOps = 4;                  // push/relabel operations per node in a node sweep
+constexpr int kDefaultTileSweeps = 8;        // local sweeps per tile visit
 constexpr int kDefaultMaxRounds = 1 << 20;   // global relabels before giving up
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -40,9 +43,9 @@ pog_status from_cuda(cudaError_t e) {
     } while (0)
 
 void set_options(pog_graph *g, const pog_options *opt) {
-    g->sweeps_per_relabel = (opt && opt->sweeps_per_relabel > 0) ? opt->sweeps_per_relabel : kDefaultSweeps;
+    g->sweeps_per_relabel = (opt && opt->sweeps_per_relabel > 0) ? opt->sweeps_per_relabel : 0;  // 0: adaptive
     g->max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : kDefaultMaxRounds;
-    g->tile_sweeps = (opt && opt->tile_sweeps > 0) ? opt->tile_sweeps : kDefaultOps;
+    g->tile_sweeps = (opt && opt->tile_sweeps > 0) ? opt->tile_sweeps : kDefaultTileSweeps;
     g->flags = opt ? opt->flags : 0;
     g->bfs_blocks = (opt && opt->bfs_blocks_per_sm > 0) ? opt->bfs_blocks_per_sm : 0;
 }
@@ -106,9 +109,11 @@ void fold_timers(pog_graph *g) {
 // termination count; returns the number of active nodes.
 pog_status global_relabel(pog_graph *g, long long &active) {
     POG_TRY(reset_field(g, &DevCounters::active));
+    POG_TRY_CUDA(cudaEventRecord(g->round_ev[0], g->stream));
     POG_TRY_CUDA(timed(g, TM_BFS, [&] {
         return pog::launch_global_relabel(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
     }));
+    POG_TRY_CUDA(cudaEventRecord(g->round_ev[1], g->stream));
     g->stats[ST_LAUNCHES] += 1;
     POG_TRY(read_counters(g));
     g->stats[ST_BFS] += g->ctr_host->max_label;  // BFS levels of this relabel
@@ -134,12 +139,22 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
     g->stats[ST_ROUNDS] = 1;
     g->stats[ST_ACTIVE0] = active;
     const bool gap = !(g->flags & POG_FLAG_NO_GAP);
-    const int half = g->sweeps_per_relabel / 2;
+    // Sweeps per global relabel: fixed when requested; otherwise chosen each round so the
+    // device time of the sweeps balances that of one global relabel, the GPU form of the
+    // paper's rule of relabelling after a fixed factor of n discharges (Section 3.3).
+    int sweeps = g->sweeps_per_relabel > 0 ? g->sweeps_per_relabel : kFirstSweeps;
     while (active > 0) {
         if (g->stats[ST_ROUNDS] >= g->max_rounds) return POG_E_NOCONVERGE;
-        for (int k = 0; k < g->sweeps_per_relabel; ++k) {
+        float gr_ms = 0.0f;
+        cudaEventElapsedTime(&gr_ms, g->round_ev[0], g->round_ev[1]);
+        const int half = sweeps / 2;
+        POG_TRY_CUDA(cudaEventRecord(g->round_ev[2], g->stream));
+        for (int k = 0; k < sweeps; ++k) {
             POG_TRY_CUDA(timed(g, TM_SWEEP, [&] {
-                return pog::launch_sweep(g->grid, g->queue_a, &g->bfs_sync->size[0], g->tile_sweeps, g->stream);
+                if (g->flags & POG_FLAG_NODE_SWEEPS)
+                    return pog::launch_sweep(g->grid, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
+                return pog::launch_tile_sweep(g->grid, g->tile_flag, g->tile_list, g->tile_work, g->tile_sweeps,
+                                              g->stream);
             }));
             if (gap && k + 1 == half) {
                 POG_TRY(reset_field(g, &DevCounters::raised));
@@ -149,10 +164,19 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
                 g->stats[ST_GAPS]++;
             }
         }
-        g->stats[ST_SWEEP] += g->sweeps_per_relabel;
-        g->stats[ST_LAUNCHES] += 2 * g->sweeps_per_relabel;
+        POG_TRY_CUDA(cudaEventRecord(g->round_ev[3], g->stream));
+        g->stats[ST_SWEEP] += sweeps;
+        g->stats[ST_LAUNCHES] += 2 * sweeps;
         POG_TRY(global_relabel(g, active));
         g->stats[ST_ROUNDS]++;
+        if (g->sweeps_per_relabel <= 0) {
+            float sw_ms = 0.0f;
+            cudaEventElapsedTime(&sw_ms, g->round_ev[2], g->round_ev[3]);
+            const float per = sw_ms / (float)sweeps;
+            float want = per > 0.0f ? kRelabelFactor * gr_ms / per : (float)kMaxSweeps;
+            want = want < (float)kFirstSweeps ? (float)kFirstSweeps : (want > (float)kMaxSweeps ? (float)kMaxSweeps : want);
+            sweeps = (int)want;
+        }
     }
     // Maximum preflow reached: extract the minimal cut, the heights and the flow value.
     POG_TRY_CUDA(timed(g, TM_CUT, [&] {
@@ -194,7 +218,8 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
     const size_t ctr = align_up(sizeof(DevCounters), 256) + (size_t)kGapLevels / 8;
     const size_t sync = align_up(sizeof(pog::BfsSync), 256);
     const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
-    g->arena_bytes = per * (arrays + 2) + heights + ctr + sync + trace;
+    const size_t tiles = align_up(sizeof(int32_t) * (size_t)pog::tile_count(g->grid_dims()), 256);
+    g->arena_bytes = per * (arrays + 2) + heights + ctr + sync + trace + 2 * tiles + 256;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -206,6 +231,13 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
         cudaFree(g->arena);
         delete g;
         return POG_E_NOMEM;
+    }
+    for (auto &ev : g->round_ev) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            ev = nullptr;
+            pog_free(g);
+            return POG_E_CUDA;
+        }
     }
     char *p = static_cast<char *>(g->arena);
     Grid &gr = g->grid;
@@ -232,9 +264,16 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
     g->trace = reinterpret_cast<pog::LevelTrace *>(p);
     p += trace;
     gr.trace = g->trace;
+    g->tile_flag = reinterpret_cast<int32_t *>(p);
+    p += tiles;
+    g->tile_list = reinterpret_cast<int32_t *>(p);
+    p += tiles;
+    g->tile_work = reinterpret_cast<int32_t *>(p);
+    p += 256;
     g->ctr = reinterpret_cast<DevCounters *>(p);
     gr.ctr = g->ctr;
     e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_flag, 0, tiles, g->stream);
     if (e == cudaSuccess) e = timed(g, TM_BUILD, [&] { return launch(gr, g->stream); });
     if (e != cudaSuccess) {
         pog_free(g);
@@ -316,6 +355,7 @@ pog_status pog_stats(const pog_graph *g, pog_stats_t *out) {
     out->gaps = g->stats[ST_GAPS];
     out->active_initial = g->stats[ST_ACTIVE0];
     out->launches = g->stats[ST_LAUNCHES] + 1;
+    out->tiles_visited = (long long)g->ctr_host->tiles_visited;
     out->nodes = g->N;
     out->state_bytes = (long long)g->arena_bytes;
     if (g->timers[TM_BUILD].used) {  // the build was timed; its events are complete after pog_maxflow
@@ -382,6 +422,8 @@ void pog_free(pog_graph *g) {
         for (int i = 0; i < t.cap; ++i) cudaEventDestroy(t.ev[i]);
         std::free(t.ev);
     }
+    for (auto ev : g->round_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(g->arena);
     cudaFreeHost(g->ctr_host);
     delete g;

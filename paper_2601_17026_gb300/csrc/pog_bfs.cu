@@ -225,7 +225,7 @@ cudaError_t coop_launch(K kernel, const Grid &g, int *qa, int *qb, BfsSync *sync
     if (!coop) return cudaErrorNotSupported;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBfsThreads, 0)) != cudaSuccess) return e;
-    const int want = blocks_per_sm > 0 ? blocks_per_sm : 2;
+    const int want = blocks_per_sm > 0 ? blocks_per_sm : 4;
     const int blocks = sms * (per_sm < want ? per_sm : want);  // co-resident by construction
     if (blocks < 1) return cudaErrorInvalidConfiguration;
     if ((e = cudaMemsetAsync(sync, 0, sizeof(BfsSync), st)) != cudaSuccess) return e;

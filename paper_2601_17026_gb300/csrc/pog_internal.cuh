@@ -40,6 +40,7 @@ struct DevCounters {
     unsigned long long excess_sum;   // sum of final excess over z >= 1
     unsigned long long active;       // active nodes (excess > 0, label < INF)
     unsigned long long raised;       // labels raised by the last gap relabel
+    unsigned long long tiles_visited;  // tile visits of the tiled sweeps
     int changed;                     // a relaxation pass changed something
     int error;                       // POG_ERR_* bits
     int gap_level;                   // first empty label level found, or 0
@@ -137,7 +138,10 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
         }
     }
 #pragma unroll
-    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = h.res[i] > 0 ? ldcg(g.lab + h.node[i]) : POG_INF;
+    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = ldcg(g.lab + h.node[i]);  // one round trip with the residuals
+#pragma unroll
+    for (int i = 0; i < kMaxArcs; ++i)
+        if (h.res[i] <= 0) h.lab[i] = POG_INF;
 }
 
 // In-arcs of v (arcs u -> v): slot 0 from above, 1 from below, 2+3d hard arc of
@@ -178,7 +182,10 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
         }
     }
 #pragma unroll
-    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = h.res[i] > 0 ? ldcg(g.lab + h.node[i]) : POG_INF;
+    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = ldcg(g.lab + h.node[i]);
+#pragma unroll
+    for (int i = 0; i < kMaxArcs; ++i)
+        if (h.res[i] <= 0) h.lab[i] = POG_INF;
 }
 
 }  // namespace pog
@@ -195,11 +202,22 @@ struct pog_graph {
     int32_t *queue_a, *queue_b;  // device [N] each: BFS frontiers
     pog::BfsSync *bfs_sync;      // device: grid barrier + frontier sizes
     pog::LevelTrace *trace;      // device [kTraceLevels]: last global relabel
+    int32_t *tile_flag;          // device [tiles]: listed in the current tiled sweep
+    int32_t *tile_list;          // device [tiles]
+    int32_t *tile_work;          // device [2]: listed tiles, next tile to take
     pog::DevCounters *ctr;       // device
     pog::DevCounters *ctr_host;  // pinned host mirror
     int solved;
     long long flow;
     int sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks;
+    pog::Grid grid_dims() const {
+        pog::Grid d{};
+        d.X = X;
+        d.Y = Y;
+        d.Z = Z;
+        return d;
+    }
+    cudaEvent_t round_ev[4];     // global relabel start/stop, sweep block start/stop
     long long stats[8];
     // POG_FLAG_TIMING: event pairs per kernel family, folded into ms[] after a sync
     struct Timer {

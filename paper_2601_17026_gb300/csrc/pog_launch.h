@@ -23,6 +23,8 @@ cudaError_t launch_backward(float *grad, const int32_t *h, const int32_t *ht, co
 cudaError_t launch_global_relabel(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
                                   cudaStream_t st);
 cudaError_t launch_cut_reach(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st);
+long long tile_count(const Grid &g);
+cudaError_t launch_tile_sweep(const Grid &g, int *flag, int *list, int *work, int local_sweeps, cudaStream_t st);
 cudaError_t launch_surface_energy(const float *cost, float scale, const int32_t *h, int B, int X, int Y, int Z,
                                   int alpha, long long *out, cudaStream_t st);
 

@@ -1,0 +1,307 @@
+// Tiled push/relabel (Section 3.2.1's column segments, mapped to thread blocks): a block
+// stages one tile of TX x TY columns x TZ heights of residual state in shared memory,
+// runs several local push/relabel sweeps on it (Algorithm 2, lock-free in the manner of
+// the node kernels), and writes the tile back. Only tiles holding an active node are
+// visited.
+//
+// Ownership rules that keep concurrent tiles consistent:
+//   * a node's label and sink residual change only in the tile that owns the node;
+//   * every arc value is stored at one node, hence staged by one tile; a neighbouring
+//     tile pushing along such an arc (or its reverse) uses a global atomic on the stored
+//     copy, and the owning tile writes its own change back as an atomic delta;
+//   * excess is likewise written back as a delta, so pushes that arrive from outside
+//     during the pass are kept.
+// Each tile only ever reads values that other tiles can move in the direction that
+// shrinks its own pushes, as in the node kernels, so the preflow stays valid.
+#include "pog_internal.cuh"
+#include "pog_launch.h"
+
+namespace pog {
+
+namespace {
+
+constexpr int TX = 4, TY = 8, TZ = 32;
+constexpr int kCols = TX * TY;         // columns per tile
+constexpr int kTileNodes = kCols * TZ;  // 1024
+constexpr int kTileThreads = 256;
+constexpr int kPerThread = kTileNodes / kTileThreads;  // 4 nodes, one column each, same z
+
+struct TileGeom {
+    int ntx, nty, ntz;  // tiles per axis
+};
+
+__device__ __forceinline__ int tile_of(const Grid &g, const TileGeom &t, int u) {
+    const int z = u % g.Z;
+    const int col = u / g.Z;
+    const int x = col / g.Y, y = col - x * g.Y;
+    return ((x / TX) * t.nty + (y / TY)) * t.ntz + z / TZ;
+}
+
+__global__ void __launch_bounds__(256) k_collect_tiles(Grid g, TileGeom t, int *flag, int *list, int *count) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
+        if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
+        const int tile = tile_of(g, t, u);
+        if (__ldcg(flag + tile)) continue;
+        if (atomicExch(flag + tile, 1) == 0) list[atomicAdd(count, 1)] = tile;
+    }
+}
+
+// Shared-memory image of a tile: current values and the values at load time (for the
+// delta write-back). Arrays are indexed by c * TZ + dz.
+struct TileSmem {
+    int lab[kTileNodes], exc[kTileNodes], snk[kTileNodes], fdn[kTileNodes];
+    int fh[4][kTileNodes];
+    int exc0[kTileNodes], fdn0[kTileNodes];
+    int fh0[4][kTileNodes];
+};
+struct TileSoft {
+    int gs[2][kTileNodes];
+    int gs0[2][kTileNodes];
+};
+
+struct Where {
+    bool in;   // the far node / stored slot lies in this tile
+    int s;     // shared index when in
+    int gidx;  // global node index
+};
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kTileThreads, 2) k_tile_push_relabel(Grid g, TileGeom tg, const int *list,
+                                                                    const int *count, int *flag, int *next,
+                                                                    int local_sweeps) {
+    extern __shared__ int4 smem_raw[];
+    TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
+    TileSoft &SS = *reinterpret_cast<TileSoft *>(reinterpret_cast<char *>(smem_raw) + sizeof(TileSmem));
+    __shared__ int tile_id;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntiles = *count;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int slot = atomicAdd(next, 1);
+            tile_id = slot < ntiles ? list[slot] : -1;
+        }
+        __syncthreads();
+        const int tile = tile_id;
+        if (tile < 0) return;
+        const int tz = tile % tg.ntz;
+        const int txy = tile / tg.ntz;
+        const int x0 = (txy / tg.nty) * TX, y0 = (txy % tg.nty) * TY, z0 = tz * TZ;
+        if (threadIdx.x == 0) flag[tile] = 0;  // the tile may be listed again by a later scan
+
+        // ---- load (coalesced: a warp reads 32 consecutive heights of one column)
+        int node[kPerThread];
+        bool own[kPerThread];
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int c = warp + 8 * k;  // column within the tile
+            const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + lane;
+            own[k] = x < g.X && y < g.Y && z < g.Z && z >= 1;
+            node[k] = own[k] ? (x * g.Y + y) * g.Z + z : -1;
+            const int s = c * TZ + lane;
+            const int u = node[k];
+            S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
+            const int e = own[k] ? ldcg(g.exc + u) : 0;
+            S.exc[s] = e;
+            S.exc0[s] = e;
+            S.snk[s] = own[k] ? ldcg(g.snk + u) : 0;
+            const int f = own[k] ? ldcg(g.fdn + u) : 0;
+            S.fdn[s] = f;
+            S.fdn0[s] = f;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const int v = own[k] ? ldcg(g.fh[d] + u) : 0;
+                S.fh[d][s] = v;
+                S.fh0[d][s] = v;
+            }
+            if (SOFT) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int v = own[k] ? ldcg(g.gs[j] + u) : 0;
+                    SS.gs[j][s] = v;
+                    SS.gs0[j][s] = v;
+                }
+            }
+        }
+        __syncthreads();
+
+        // locate node (x, y, z) relative to the tile
+        auto where = [&](int x, int y, int z) {
+            Where w;
+            w.gidx = (x * g.Y + y) * g.Z + z;
+            w.in = x >= x0 && x < x0 + TX && y >= y0 && y < y0 + TY && z >= z0 && z < z0 + TZ;
+            w.s = ((x - x0) * TY + (y - y0)) * TZ + (z - z0);
+            return w;
+        };
+        auto lab_of = [&](const Where &w) { return w.in ? S.lab[w.s] : ldcg(g.lab + w.gidx); };
+
+        // ---- local sweeps, until none of the tile's nodes is active
+        for (int it = 0; it < local_sweeps; ++it) {
+            int busy = 0;
+#pragma unroll 1
+            for (int k = 0; k < kPerThread; ++k) {
+                if (!own[k]) continue;
+                const int c = warp + 8 * k;
+                const int s = c * TZ + lane;
+                const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + lane;
+                const int e = S.exc[s];
+                const int h = S.lab[s];
+                if (e <= 0 || h >= POG_INF) continue;
+                busy = 1;
+                const int sk = S.snk[s];
+                if (sk > 0) {
+                    if (h > 0) {
+                        const int d = e < sk ? e : sk;
+                        S.snk[s] = sk - d;
+                        atomicSub(&S.exc[s], d);
+                    } else {
+                        S.lab[s] = 1;
+                    }
+                    continue;
+                }
+                // gather: residual and far-end label of every arc (see gather_out)
+                int best = POG_INF, bk = -1, bres = 0, bd = 0;
+                Where bw;
+                bw.in = false;
+                bw.s = 0;
+                bw.gidx = 0;
+                auto consider = [&](int kind, int dir, const Where &w, int res) {
+                    if (res <= 0) return;
+                    const int l = lab_of(w);
+                    if (l < best) {
+                        best = l;
+                        bk = kind;
+                        bd = dir;
+                        bw = w;
+                        bres = res;
+                    }
+                };
+                if (z >= 2) consider(ARC_DOWN, 0, where(x, y, z - 1), POG_CAP_INF - S.fdn[s]);
+                if (z + 1 < g.Z) {
+                    const Where w = where(x, y, z + 1);
+                    consider(ARC_UP, 0, w, w.in ? S.fdn[w.s] : ldcg(g.fdn + w.gidx));
+                }
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    const int xq = x + (d == 0 ? -1 : d == 1 ? 1 : 0);
+                    const int yq = y + (d == 2 ? -1 : d == 3 ? 1 : 0);
+                    if (xq < 0 || xq >= g.X || yq < 0 || yq >= g.Y) continue;
+                    if (z - g.delta >= 1) consider(ARC_HOUT, d, where(xq, yq, z - g.delta), POG_CAP_INF - S.fh[d][s]);
+                    if (z + g.delta < g.Z) {
+                        const Where w = where(xq, yq, z + g.delta);
+                        consider(ARC_HIN, d, w, w.in ? S.fh[d ^ 1][w.s] : ldcg(g.fh[d ^ 1] + w.gidx));
+                    }
+                    if (SOFT) {
+                        const Where w = where(xq, yq, z);
+                        int r;
+                        if (d & 1) r = g.alpha - SS.gs[d >> 1][s];
+                        else r = g.alpha + (w.in ? SS.gs[d >> 1][w.s] : ldcg(g.gs[d >> 1] + w.gidx));
+                        consider(ARC_SOFT, d, w, r);
+                    }
+                }
+                if (bk < 0 || h <= best) {
+                    S.lab[s] = best >= POG_INF - 1 ? POG_INF : best + 1;
+                    continue;
+                }
+                const int delta = e < bres ? e : bres;
+                int sat = 0;
+                switch (bk) {
+                    case ARC_DOWN: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
+                    case ARC_UP:
+                        if (bw.in) atomicSub(&S.fdn[bw.s], delta);
+                        else atomicSub(g.fdn + bw.gidx, delta);
+                        break;
+                    case ARC_HOUT: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
+                    case ARC_HIN:
+                        if (bw.in) atomicSub(&S.fh[bd ^ 1][bw.s], delta);
+                        else atomicSub(g.fh[bd ^ 1] + bw.gidx, delta);
+                        break;
+                    default:
+                        if (bd & 1) atomicAdd(&SS.gs[bd >> 1][s], delta);
+                        else if (bw.in) atomicSub(&SS.gs[bd >> 1][bw.s], delta);
+                        else atomicSub(g.gs[bd >> 1] + bw.gidx, delta);
+                        break;
+                }
+                atomicSub(&S.exc[s], delta);
+                int old;
+                if (bw.in) old = atomicAdd(&S.exc[bw.s], delta);
+                else old = atomicAdd(g.exc + bw.gidx, delta);
+                if (old > 0x7fffffff - delta) sat = 1;
+                if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
+            }
+            if (!__syncthreads_or(busy)) break;
+        }
+        if (threadIdx.x == 0) atomicAdd(&g.ctr->tiles_visited, 1ull);
+
+        // ---- write back: owner-only words by store, shared words as deltas
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            if (!own[k]) continue;
+            const int s = (warp + 8 * k) * TZ + lane;
+            const int u = node[k];
+            g.lab[u] = S.lab[s];
+            g.snk[u] = S.snk[s];
+            int d = S.exc[s] - S.exc0[s];
+            if (d) atomicAdd(g.exc + u, d);
+            d = S.fdn[s] - S.fdn0[s];
+            if (d) atomicAdd(g.fdn + u, d);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                d = S.fh[j][s] - S.fh0[j][s];
+                if (d) atomicAdd(g.fh[j] + u, d);
+            }
+            if (SOFT) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    d = SS.gs[j][s] - SS.gs0[j][s];
+                    if (d) atomicAdd(g.gs[j] + u, d);
+                }
+            }
+        }
+    }
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 148;
+    }
+    return sms;
+}
+
+}  // namespace
+
+long long tile_count(const Grid &g) {
+    return (long long)((g.X + TX - 1) / TX) * ((g.Y + TY - 1) / TY) * ((g.Z + TZ - 1) / TZ);
+}
+
+// One tiled sweep: list the tiles that hold an active node, then let persistent blocks
+// take tiles from the list. `work` holds [count, next]; `flag` is one int per tile and
+// must start zeroed (each visited tile clears its own flag).
+cudaError_t launch_tile_sweep(const Grid &g, int *flag, int *list, int *work, int local_sweeps, cudaStream_t st) {
+    TileGeom t{(g.X + TX - 1) / TX, (g.Y + TY - 1) / TY, (g.Z + TZ - 1) / TZ};
+    cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
+    k_collect_tiles<<<sms * 8, 256, 0, st>>>(g, t, flag, list, work);
+    const bool soft = g.gs[0] != nullptr;
+    const size_t smem = sizeof(TileSmem) + (soft ? sizeof(TileSoft) : 0);
+    static bool configured[2] = {false, false};
+    if (!configured[soft]) {
+        e = soft ? cudaFuncSetAttribute(k_tile_push_relabel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_tile_push_relabel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[soft] = true;
+    }
+    const int blocks = sms * 2;
+    if (soft)
+        k_tile_push_relabel<true><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1, local_sweeps);
+    else
+        k_tile_push_relabel<false><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1, local_sweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace pog

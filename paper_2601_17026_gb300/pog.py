@@ -27,6 +27,7 @@ POG_E_STATE = 7
 POG_FLAG_NO_GAP = 1
 POG_FLAG_TIMING = 2
 POG_FLAG_NO_PREPUSH = 4
+POG_FLAG_NODE_SWEEPS = 8
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
@@ -47,7 +48,7 @@ class pog_options(ctypes.Structure):
 
 class pog_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("rounds", "sweeps", "bfs_passes", "cut_passes", "gaps",
-                                               "active_initial", "nodes", "state_bytes", "launches")] + \
+                                               "active_initial", "nodes", "state_bytes", "launches", "tiles_visited")] + \
                [(n, ctypes.c_double) for n in ("sweep_ms", "bfs_ms", "cut_ms", "build_ms")]
 
 

@@ -56,4 +56,4 @@ def test_header_compiles_as_c(tmp_path):
 
 def test_options_struct_layout():
     assert ctypes.sizeof(pog.pog_options) == 32
-    assert ctypes.sizeof(pog.pog_stats_t) == 104
+    assert ctypes.sizeof(pog.pog_stats_t) == 112
