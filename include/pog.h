@@ -63,7 +63,8 @@ typedef struct {
     int32_t tile_sweeps;        /* local push/relabel sweeps per shared-memory tile visit */
     int32_t flags;              /* POG_FLAG_* bits */
     int32_t bfs_blocks_per_sm;  /* resident blocks per SM of the cooperative BFS launches */
-    int32_t reserved[3];
+    float relabel_factor;       /* adaptive mode: sweep time per round / global relabel time */
+    int32_t reserved[2];
 } pog_options;
 
 #define POG_FLAG_NO_GAP 1     /* disable the gap heuristic between global relabels */

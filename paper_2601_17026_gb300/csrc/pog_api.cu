@@ -48,6 +48,7 @@ void set_options(pog_graph *g, const pog_options *opt) {
     g->tile_sweeps = (opt && opt->tile_sweeps > 0) ? opt->tile_sweeps : kDefaultTileSweeps;
     g->flags = opt ? opt->flags : 0;
     g->bfs_blocks = (opt && opt->bfs_blocks_per_sm > 0) ? opt->bfs_blocks_per_sm : 0;
+    g->relabel_factor = (opt && opt->relabel_factor > 0.0f) ? opt->relabel_factor : kRelabelFactor;
 }
 
 template <class T>
@@ -173,7 +174,7 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
             float sw_ms = 0.0f;
             cudaEventElapsedTime(&sw_ms, g->round_ev[2], g->round_ev[3]);
             const float per = sw_ms / (float)sweeps;
-            float want = per > 0.0f ? kRelabelFactor * gr_ms / per : (float)kMaxSweeps;
+            float want = per > 0.0f ? g->relabel_factor * gr_ms / per : (float)kMaxSweeps;
             want = want < (float)kFirstSweeps ? (float)kFirstSweeps : (want > (float)kMaxSweeps ? (float)kMaxSweeps : want);
             sweeps = (int)want;
         }

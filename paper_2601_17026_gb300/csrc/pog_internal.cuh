@@ -210,6 +210,7 @@ struct pog_graph {
     int solved;
     long long flow;
     int sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks;
+    float relabel_factor;
     pog::Grid grid_dims() const {
         pog::Grid d{};
         d.X = X;

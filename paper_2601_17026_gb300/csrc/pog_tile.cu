@@ -67,7 +67,7 @@ struct Where {
 };
 
 template <bool SOFT>
-__global__ void __launch_bounds__(kTileThreads, 2) k_tile_push_relabel(Grid g, TileGeom tg, const int *list,
+__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, TileGeom tg, const int *list,
                                                                     const int *count, int *flag, int *next,
                                                                     int local_sweeps) {
     extern __shared__ int4 smem_raw[];
@@ -134,9 +134,13 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_push_relabel(Grid g, T
             w.s = ((x - x0) * TY + (y - y0)) * TZ + (z - z0);
             return w;
         };
-        auto lab_of = [&](const Where &w) { return w.in ? S.lab[w.s] : ldcg(g.lab + w.gidx); };
+        auto lab_of = [&](const Where &w) { return w.in ? ((volatile int *)S.lab)[w.s] : ldcg(g.lab + w.gidx); };
 
-        // ---- local sweeps, until none of the tile's nodes is active
+        // ---- local sweeps. Warps run them without block barriers (shared atomics keep
+        // the tile consistent, and volatile reads see other warps' progress); a warp stops
+        // early once none of its nodes is active.
+        volatile int *vexc = S.exc;
+        volatile int *vlab = S.lab;
         for (int it = 0; it < local_sweeps; ++it) {
             int busy = 0;
 #pragma unroll 1
@@ -145,11 +149,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_push_relabel(Grid g, T
                 const int c = warp + 8 * k;
                 const int s = c * TZ + lane;
                 const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + lane;
-                const int e = S.exc[s];
-                const int h = S.lab[s];
+                const int e = vexc[s];
+                const int h = vlab[s];
                 if (e <= 0 || h >= POG_INF) continue;
                 busy = 1;
-                const int sk = S.snk[s];
+                const int sk = ((volatile int *)S.snk)[s];
                 if (sk > 0) {
                     if (h > 0) {
                         const int d = e < sk ? e : sk;
@@ -177,26 +181,30 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_push_relabel(Grid g, T
                         bres = res;
                     }
                 };
-                if (z >= 2) consider(ARC_DOWN, 0, where(x, y, z - 1), POG_CAP_INF - S.fdn[s]);
+                volatile int *vfdn = S.fdn;
+                if (z >= 2) consider(ARC_DOWN, 0, where(x, y, z - 1), POG_CAP_INF - vfdn[s]);
                 if (z + 1 < g.Z) {
                     const Where w = where(x, y, z + 1);
-                    consider(ARC_UP, 0, w, w.in ? S.fdn[w.s] : ldcg(g.fdn + w.gidx));
+                    consider(ARC_UP, 0, w, w.in ? vfdn[w.s] : ldcg(g.fdn + w.gidx));
                 }
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
                     const int xq = x + (d == 0 ? -1 : d == 1 ? 1 : 0);
                     const int yq = y + (d == 2 ? -1 : d == 3 ? 1 : 0);
                     if (xq < 0 || xq >= g.X || yq < 0 || yq >= g.Y) continue;
-                    if (z - g.delta >= 1) consider(ARC_HOUT, d, where(xq, yq, z - g.delta), POG_CAP_INF - S.fh[d][s]);
+                    volatile int *vfh = S.fh[d];
+                    volatile int *vfho = S.fh[d ^ 1];
+                    if (z - g.delta >= 1) consider(ARC_HOUT, d, where(xq, yq, z - g.delta), POG_CAP_INF - vfh[s]);
                     if (z + g.delta < g.Z) {
                         const Where w = where(xq, yq, z + g.delta);
-                        consider(ARC_HIN, d, w, w.in ? S.fh[d ^ 1][w.s] : ldcg(g.fh[d ^ 1] + w.gidx));
+                        consider(ARC_HIN, d, w, w.in ? vfho[w.s] : ldcg(g.fh[d ^ 1] + w.gidx));
                     }
                     if (SOFT) {
+                        volatile int *vgs = SS.gs[d >> 1];
                         const Where w = where(xq, yq, z);
                         int r;
-                        if (d & 1) r = g.alpha - SS.gs[d >> 1][s];
-                        else r = g.alpha + (w.in ? SS.gs[d >> 1][w.s] : ldcg(g.gs[d >> 1] + w.gidx));
+                        if (d & 1) r = g.alpha - vgs[s];
+                        else r = g.alpha + (w.in ? vgs[w.s] : ldcg(g.gs[d >> 1] + w.gidx));
                         consider(ARC_SOFT, d, w, r);
                     }
                 }
@@ -230,8 +238,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_push_relabel(Grid g, T
                 if (old > 0x7fffffff - delta) sat = 1;
                 if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
             }
-            if (!__syncthreads_or(busy)) break;
+            if (!__any_sync(0xffffffffu, busy)) break;
         }
+        __syncthreads();
         if (threadIdx.x == 0) atomicAdd(&g.ctr->tiles_visited, 1ull);
 
         // ---- write back: owner-only words by store, shared words as deltas
@@ -296,7 +305,7 @@ cudaError_t launch_tile_sweep(const Grid &g, int *flag, int *list, int *work, in
         if (e != cudaSuccess) return e;
         configured[soft] = true;
     }
-    const int blocks = sms * 2;
+    const int blocks = sms * 3;
     if (soft)
         k_tile_push_relabel<true><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1, local_sweeps);
     else

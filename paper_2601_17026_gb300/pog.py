@@ -43,7 +43,7 @@ class PogError(RuntimeError):
 class pog_options(ctypes.Structure):
     _fields_ = [("sweeps_per_relabel", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("tile_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32), ("bfs_blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("relabel_factor", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
 
 
 class pog_stats_t(ctypes.Structure):
@@ -123,8 +123,9 @@ def _dev(t, dtype, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_options(sweeps_per_relabel=0, max_rounds=0, tile_sweeps=0, flags=0, bfs_blocks_per_sm=0) -> pog_options:
-    return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks_per_sm)
+def make_options(sweeps_per_relabel=0, max_rounds=0, tile_sweeps=0, flags=0, bfs_blocks_per_sm=0,
+                 relabel_factor=0.0) -> pog_options:
+    return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks_per_sm, relabel_factor)
 
 
 def pog_strerror(status: int) -> str:
