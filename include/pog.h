@@ -243,6 +243,48 @@ typedef struct {
 POG_API pog_status pog_solve_batch(int32_t n, const pog_volume *vols, const pog_options *opt,
                            void *stream, int64_t *flows_out, int32_t *const *heights_dev);
 
+/*
+ * Solve one volume without allocating anything (the paper has no counterpart; this
+ * entry point exists for callers of this library, not for the method).
+ *
+ * Who needs it: code that may not call cudaMalloc or any other allocating routine.
+ * Examples are a host framework that owns every byte of device memory through its own
+ * pool and forbids libraries from allocating behind its back, and latency-bound loops
+ * in which cudaMalloc's implicit device-wide synchronisation cannot be afforded.
+ * pog_build allocates its state with cudaMalloc (and pinned host memory and events);
+ * this call instead does the whole solve (what pog_build, pog_maxflow and pog_surface
+ * do together) with every scratch word in one fixed device array that the library
+ * defines at file scope, POG_NOALLOC_SCRATCH_BYTES (32 MiB) in size. Every GPU on which
+ * the library is loaded holds that array until the process exits.
+ *
+ * Limit: the volume's scratch must fit the array. It needs 48 bytes per node with
+ * alpha > 0 (40 with alpha == 0) plus about 130 KiB, so about 690,000 nodes with a soft
+ * penalty or 830,000 without. Larger volumes return POG_E_INVALID; use pog_build.
+ *
+ *   cost_dev    : device, int32 [X][Y][Z], as for pog_build.
+ *   X, Y, Z, delta, alpha, opt : as for pog_build. sweeps_per_relabel is fixed here
+ *                 (default 64): this path keeps no timing events, so the adaptive
+ *                 choice is off. POG_FLAG_TIMING and the relabel trace are ignored.
+ *   stream      : cudaStream_t for all device work.
+ *   flow_out    : host, receives the max-flow value.
+ *   heights_dev : device, int32 [X][Y], receives the surface heights (caller-owned).
+ * Blocks until the stream has finished the solve. Allocates no device or host memory,
+ * creates no events and calls no allocating library routine.
+ *
+ * Set-up: the first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call before any
+ * stream capture begins on the device.
+ *
+ * Sharing: every call on a device uses the same array, which keeps the last call's
+ * contents (each call clears what must start at zero). Calls whose device work
+ * overlaps — on two streams, or from two host threads — race on the array and give
+ * wrong results; serialise them.
+ */
+#define POG_NOALLOC_SCRATCH_BYTES (32u << 20)
+POG_API pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                                     int32_t alpha, const pog_options *opt, void *stream, int64_t *flow_out,
+                                     int32_t *heights_dev);
+
 #ifdef __cplusplus
 }
 #endif

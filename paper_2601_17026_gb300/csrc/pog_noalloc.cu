@@ -1,0 +1,174 @@
+// pog_solve_noalloc: the whole solve (what pog_build + pog_maxflow + pog_surface do)
+// for callers that must not allocate, with every scratch word in one file-scope device
+// array instead of memory from cudaMalloc. See include/pog.h for the contract.
+#include <cstddef>
+#include <cstring>
+#include <mutex>
+
+#include "pog.h"
+#include "pog_internal.cuh"
+#include "pog_launch.h"
+
+namespace {
+
+// The scratch array. In host code its name is only a stand-in for the device object:
+// its device address comes from cudaGetSymbolAddress (once per device, below).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[POG_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kGapLevels = 1 << 20;        // labels tracked by the gap bitmap
+constexpr int kSweepsPerRelabel = 64;      // fixed: this path keeps no timing events
+constexpr int kTileSweeps = 8;
+constexpr int kNodeOps = 4;
+constexpr int kMaxRounds = 1 << 20;
+constexpr int kMaxDevices = 64;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+std::mutex g_symbol_lock;
+void *g_symbol_addr[kMaxDevices] = {nullptr};
+
+pog_status from_cuda(cudaError_t e) { return e == cudaSuccess ? POG_OK : POG_E_CUDA; }
+
+#define NA_TRY_CUDA(expr)                                \
+    do {                                                 \
+        const pog_status _s = from_cuda((expr));         \
+        if (_s != POG_OK) return _s;                     \
+    } while (0)
+#define NA_TRY(expr)                                     \
+    do {                                                 \
+        const pog_status _s = (expr);                    \
+        if (_s != POG_OK) return _s;                     \
+    } while (0)
+
+// Device address of the scratch array on the current device (set up on first use).
+pog_status scratch_address(void **out) {
+    int dev = 0;
+    NA_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return POG_E_INVALID;
+    std::lock_guard<std::mutex> lock(g_symbol_lock);
+    if (!g_symbol_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return POG_E_CUDA;
+        g_symbol_addr[dev] = p;
+    }
+    *out = g_symbol_addr[dev];
+    return POG_OK;
+}
+
+struct Carve {
+    char *p;
+    size_t used;
+    template <class T>
+    T *take(size_t bytes) {
+        T *r = reinterpret_cast<T *>(p + used);
+        used += align_up(bytes, 256);
+        return r;
+    }
+};
+
+// Bytes of scratch a volume needs (the same words as the allocating path, minus the
+// heights, which go straight to the caller's buffer, and the relabel trace).
+size_t scratch_bytes(int X, int Y, int Z, int alpha) {
+    const size_t N = (size_t)X * Y * Z;
+    const int arrays = alpha > 0 ? 10 : 8;
+    pog::Grid dims{};
+    dims.X = X;
+    dims.Y = Y;
+    dims.Z = Z;
+    const size_t tiles = (size_t)pog::tile_count(dims);
+    return (arrays + 2) * align_up(N * 4, 256) + 2 * align_up(tiles * 4, 256) + 256 +
+           align_up(sizeof(pog::BfsSync), 256) + align_up(sizeof(pog::DevCounters), 256) + kGapLevels / 8;
+}
+
+pog_status read_counters(const pog::Grid &g, pog::DevCounters &host, cudaStream_t st) {
+    NA_TRY_CUDA(cudaMemcpyAsync(&host, g.ctr, sizeof(host), cudaMemcpyDeviceToHost, st));
+    NA_TRY_CUDA(cudaStreamSynchronize(st));
+    if (host.error & POG_ERR_TIMEOUT) return POG_E_TIMEOUT;
+    if (host.error) return POG_E_OVERFLOW;
+    return POG_OK;
+}
+
+}  // namespace
+
+extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                                        int32_t alpha, const pog_options *opt, void *stream, int64_t *flow_out,
+                                        int32_t *heights_dev) {
+    if (!cost_dev || !flow_out || !heights_dev || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 ||
+        alpha >= (1 << 30))
+        return POG_E_INVALID;
+    if ((long long)X * Y * Z >= (1ll << 31) - 64) return POG_E_INVALID;
+    if (scratch_bytes(X, Y, Z, alpha) > (size_t)POG_NOALLOC_SCRATCH_BYTES) return POG_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *base = nullptr;
+    NA_TRY(scratch_address(&base));
+
+    const int sweeps = (opt && opt->sweeps_per_relabel > 0) ? opt->sweeps_per_relabel : kSweepsPerRelabel;
+    const int tile_sweeps = (opt && opt->tile_sweeps > 0) ? opt->tile_sweeps : kTileSweeps;
+    const int max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : kMaxRounds;
+    const int flags = opt ? opt->flags : 0;
+    const int bfs_blocks = (opt && opt->bfs_blocks_per_sm > 0) ? opt->bfs_blocks_per_sm : 0;
+
+    const size_t N = (size_t)X * Y * Z;
+    pog::Grid g{};
+    g.X = X;
+    g.Y = Y;
+    g.Z = Z;
+    g.delta = delta;
+    g.alpha = alpha;
+    g.N = (int)N;
+    Carve c{static_cast<char *>(base), 0};
+    g.lab = c.take<int32_t>(N * 4);
+    g.exc = c.take<int32_t>(N * 4);
+    g.snk = c.take<int32_t>(N * 4);
+    g.fdn = c.take<int32_t>(N * 4);
+    for (auto &f : g.fh) f = c.take<int32_t>(N * 4);
+    for (auto &s : g.gs) s = alpha > 0 ? c.take<int32_t>(N * 4) : nullptr;
+    int32_t *queue_a = c.take<int32_t>(N * 4);
+    int32_t *queue_b = c.take<int32_t>(N * 4);
+    const size_t tiles = (size_t)pog::tile_count(g);
+    int32_t *tile_flag = c.take<int32_t>(tiles * 4);
+    int32_t *tile_list = c.take<int32_t>(tiles * 4);
+    int32_t *tile_work = c.take<int32_t>(256);
+    pog::BfsSync *sync = c.take<pog::BfsSync>(sizeof(pog::BfsSync));
+    g.ctr = c.take<pog::DevCounters>(sizeof(pog::DevCounters));
+    unsigned int *gap_bits = c.take<unsigned int>(kGapLevels / 8);
+    g.trace = nullptr;
+
+    // The array keeps the previous call's contents: clear what must start at zero.
+    NA_TRY_CUDA(cudaMemsetAsync(g.ctr, 0, sizeof(pog::DevCounters), st));
+    NA_TRY_CUDA(cudaMemsetAsync(tile_flag, 0, tiles * 4, st));
+    NA_TRY_CUDA(pog::launch_build_i32(g, cost_dev, st));
+
+    pog::DevCounters host;
+    std::memset(&host, 0, sizeof host);
+    NA_TRY(read_counters(g, host, st));
+    if (!(flags & POG_FLAG_NO_PREPUSH)) NA_TRY_CUDA(pog::launch_column_prepush(g, st));
+    const size_t active_off = offsetof(pog::DevCounters, active);
+    for (int round = 0;; ++round) {
+        NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + active_off, 0, sizeof(host.active), st));
+        NA_TRY_CUDA(pog::launch_global_relabel(g, queue_a, queue_b, sync, bfs_blocks, st));
+        NA_TRY(read_counters(g, host, st));
+        if (host.active == 0) break;
+        if (round + 1 >= max_rounds) return POG_E_NOCONVERGE;
+        for (int k = 0; k < sweeps; ++k) {
+            if (flags & POG_FLAG_NODE_SWEEPS)
+                NA_TRY_CUDA(pog::launch_sweep(g, queue_a, &sync->size[0], kNodeOps, st));
+            else
+                NA_TRY_CUDA(pog::launch_tile_sweep(g, tile_flag, tile_list, tile_work, tile_sweeps, st));
+            if (!(flags & POG_FLAG_NO_GAP) && k + 1 == sweeps / 2) {
+                NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + offsetof(pog::DevCounters, max_label),
+                                            0, sizeof(int), st));
+                NA_TRY_CUDA(pog::launch_gap(g, gap_bits, kGapLevels, st));
+            }
+        }
+    }
+    NA_TRY_CUDA(pog::launch_cut_reach(g, queue_a, queue_b, sync, bfs_blocks, st));
+    NA_TRY_CUDA(pog::launch_heights(g, heights_dev, st));
+    NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + offsetof(pog::DevCounters, excess_sum), 0,
+                                sizeof(host.excess_sum), st));
+    NA_TRY_CUDA(pog::launch_excess_sum(g, st));
+    NA_TRY(read_counters(g, host, st));
+    *flow_out = (long long)host.bottom_const + (long long)host.src_total - (long long)host.excess_sum;
+    return POG_OK;
+}

@@ -31,7 +31,7 @@ POG_FLAG_NODE_SWEEPS = 8
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
-            "pog_surface_energy", "pog_solve_batch"]
+            "pog_surface_energy", "pog_solve_batch", "pog_solve_noalloc"]
 
 
 class PogError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
             "pog_quantise": [vp, vp, i64, f32, vp],
             "pog_backward": [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp],
             "pog_solve_batch": [i32, ctypes.POINTER(pog_volume), opts, vp, i64p, ctypes.POINTER(vp)],
+            "pog_solve_noalloc": [vp, i32, i32, i32, i32, i32, opts, vp, i64p, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -318,6 +319,19 @@ def pog_solve_batch(costs, deltas, alphas, options: pog_options | None = None, s
     _check(load().pog_solve_batch(n, vols, ctypes.byref(options) if options else None, _stream(stream), flows,
                                   hptrs), "pog_solve_batch")
     return [int(flows[i]) for i in range(n)], heights
+
+
+def pog_solve_noalloc(cost, delta: int, alpha: int, heights, options: pog_options | None = None, stream=None) -> int:
+    """Whole solve with the library's fixed scratch array (no allocation inside the call);
+    `heights` is a caller-owned int32 CUDA tensor [X, Y]. Returns the flow value."""
+    import torch
+
+    X, Y, Z = cost.shape
+    flow = ctypes.c_int64(0)
+    _check(load().pog_solve_noalloc(_dev(cost, torch.int32, "cost"), X, Y, Z, int(delta), int(alpha),
+                                    ctypes.byref(options) if options else None, _stream(stream), ctypes.byref(flow),
+                                    _dev(heights, torch.int32, "heights")), "pog_solve_noalloc")
+    return int(flow.value)
 
 
 def solve(cost, delta: int, alpha: int, options: pog_options | None = None, stream=None):
