@@ -146,13 +146,19 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     __graft_entry__.build()
+    from paper_2601_17026_gb300 import autotune
+
     vol = _workload(args.workload)
     X, Y, Z = vol.cost.shape
     N = vol.n
     host = torch.from_numpy(vol.cost).pin_memory()
     dev = host.cuda()
     stream = torch.cuda.current_stream()
-    opts = pog.make_options(flags=pog.POG_FLAG_TIMING)
+    params = autotune.tuned_params(X, Y, Z, vol.delta, vol.alpha)
+    if args.sweeps_per_relabel is not None:
+        params["sweeps_per_relabel"] = args.sweeps_per_relabel
+    opts = pog.make_options(flags=pog.POG_FLAG_TIMING, **params)
+    plain_opts = pog.make_options(**params)
 
     def step(src_dev):
         with pog.pog_build(src_dev, vol.delta, vol.alpha, opts) as g:
@@ -193,7 +199,7 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(args.steps):
         d = host.to("cuda", non_blocking=True)
-        with pog.pog_build(d, vol.delta, vol.alpha) as g:
+        with pog.pog_build(d, vol.delta, vol.alpha, plain_opts) as g:
             pog.pog_maxflow(g)  # flow value: 8 bytes read back
             hbuf.copy_(pog.pog_surface(g), non_blocking=True)
     e1.record(stream)
@@ -232,7 +238,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"{X}x{Y}x{Z} layered-horizon volume, delta={vol.delta}, alpha={vol.alpha}",
-                   "nodes": N, "state_bytes": int(st0["state_bytes"]),
+                   "nodes": N, "state_bytes": int(st0["state_bytes"]), "params": params,
                    "l2": "inputs larger than L2 (cost 4N B, state ~%d B/node)" % S,
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
@@ -250,9 +256,78 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, vol)
+    if args.extras:
+        line["batched"] = batched_leg(args)
+        line["differentiable"] = differentiable_leg(args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def batched_leg(args, warmup=1, steps=1):
+    """The 64 uneven volumes through pog_solve_batch (inputs resident), aggregate Mnodes/s;
+    flows checked against the oracle's stored values when tests/golden/batch.json exists."""
+    import hashlib
+
+    import torch
+
+    from paper_2601_17026_gb300 import pog, synth
+
+    vols = synth.batch_volumes()
+    costs = [torch.from_numpy(v.cost).cuda() for v in vols]
+    deltas = [v.delta for v in vols]
+    alphas = [v.alpha for v in vols]
+    for _ in range(warmup):
+        pog.pog_solve_batch(costs, deltas, alphas)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        flows, heights = pog.pog_solve_batch(costs, deltas, alphas)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / steps
+    n = sum(v.n for v in vols)
+    out = {"value": round(n / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2), "volumes": len(vols),
+           "nodes": n, "driver": "volumes in turn on one stream"}
+    gold = os.path.join(ROOT, "tests", "golden", "batch.json")
+    if os.path.exists(gold):
+        with open(gold) as f:
+            ref = json.load(f)["volumes"]
+        ok = 0
+        for r, fl, h in zip(ref, flows, heights):
+            hh = hashlib.sha256(h.cpu().numpy().astype(np.int32).tobytes()).hexdigest()
+            ok += int(r["flow"] == fl and r["heights_sha256"] == hh)
+        out["oracle_parity"] = f"{ok}/{len(ref)} volumes bit-exact"
+    return out
+
+
+def differentiable_leg(args, warmup=1, steps=1):
+    """16 float volumes of 128^3: quantise + solve + structured-hinge second solve + one-hot
+    backward, aggregate Mnodes/s of the volumes processed."""
+    import torch
+
+    from paper_2601_17026_gb300 import autograd as pag
+    from paper_2601_17026_gb300 import synth
+
+    fc = torch.from_numpy(synth.diff_volumes_f32()).cuda()
+    B, X, Y, Z = fc.shape
+    ht = torch.full((B, X, Y), Z // 2, dtype=torch.int32, device="cuda")  # a flat target surface
+
+    def step():
+        x = fc.clone().requires_grad_(True)
+        e, loss, h, hh = pag.solve_with_hinge(x, ht, synth.DIFF_DELTA, synth.DIFF_ALPHA)
+        (e.sum() + loss.sum()).backward()
+        return x.grad
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / steps
+    return {"value": round(B * X * Y * Z / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2),
+            "step": "forward (energy solve + loss-augmented solve) + backward", "volumes": B}
 
 
 def _crop(vol, X, Y):
@@ -312,6 +387,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="seismic", choices=["seismic", "medium", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps-per-relabel", type=int, default=None,
+                    help="fix the sweeps per global relabel (0 = adaptive); default: the tuned value")
+    ap.add_argument("--extras", dest="extras", action="store_true", default=True,
+                    help="also time the batched and differentiable workloads (default)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

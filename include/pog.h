@@ -64,7 +64,9 @@ typedef struct {
     int32_t flags;              /* POG_FLAG_* bits */
     int32_t bfs_blocks_per_sm;  /* resident blocks per SM of the cooperative BFS launches */
     float relabel_factor;       /* adaptive mode: sweep time per round / global relabel time */
-    int32_t reserved[2];
+    int32_t tile_shape;         /* 0: 4x8 columns x 32 heights, 1: 8x8x16, 2: 4x4x64, 3: 2x4x128 */
+    int32_t bfs_bottom_up_ratio; /* BFS level runs bottom-up when frontier * ratio > unlabelled
+                                    nodes; 0 = default (8), < 0 = always top-down */
 } pog_options;
 
 #define POG_FLAG_NO_GAP 1     /* disable the gap heuristic between global relabels */

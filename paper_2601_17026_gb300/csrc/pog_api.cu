@@ -22,6 +22,7 @@ constexpr float kRelabelFactor = 1.0f;       // sweep time per round / global re
 constexpr int kNodeOps = 4;                  // push/relabel operations per node in a node sweep
 constexpr int kDefaultTileSweeps = 8;        // local sweeps per tile visit
 constexpr int kDefaultMaxRounds = 1 << 20;   // global relabels before giving up
+constexpr int kBottomUpRatio = 8;            // BFS level bottom-up when frontier * 8 > unlabelled nodes
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -49,6 +50,9 @@ void set_options(pog_graph *g, const pog_options *opt) {
     g->flags = opt ? opt->flags : 0;
     g->bfs_blocks = (opt && opt->bfs_blocks_per_sm > 0) ? opt->bfs_blocks_per_sm : 0;
     g->relabel_factor = (opt && opt->relabel_factor > 0.0f) ? opt->relabel_factor : kRelabelFactor;
+    g->tile_shape = (opt && opt->tile_shape > 0 && opt->tile_shape < pog::kTileShapes) ? opt->tile_shape : 0;
+    g->bu_ratio = !opt || opt->bfs_bottom_up_ratio == 0 ? kBottomUpRatio
+                                                         : (opt->bfs_bottom_up_ratio < 0 ? 0 : opt->bfs_bottom_up_ratio);
 }
 
 template <class T>
@@ -112,7 +116,8 @@ pog_status global_relabel(pog_graph *g, long long &active) {
     POG_TRY(reset_field(g, &DevCounters::active));
     POG_TRY_CUDA(cudaEventRecord(g->round_ev[0], g->stream));
     POG_TRY_CUDA(timed(g, TM_BFS, [&] {
-        return pog::launch_global_relabel(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
+        return pog::launch_global_relabel(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->bu_ratio,
+                                          g->stream);
     }));
     POG_TRY_CUDA(cudaEventRecord(g->round_ev[1], g->stream));
     g->stats[ST_LAUNCHES] += 1;
@@ -154,8 +159,8 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
             POG_TRY_CUDA(timed(g, TM_SWEEP, [&] {
                 if (g->flags & POG_FLAG_NODE_SWEEPS)
                     return pog::launch_sweep(g->grid, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
-                return pog::launch_tile_sweep(g->grid, g->tile_flag, g->tile_list, g->tile_work, g->tile_sweeps,
-                                              g->stream);
+                return pog::launch_tile_sweep(g->grid, g->tile_shape, g->tile_flag, g->tile_list, g->tile_work,
+                                              g->tile_sweeps, g->stream);
             }));
             if (gap && k + 1 == half) {
                 POG_TRY(reset_field(g, &DevCounters::raised));
@@ -219,7 +224,7 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
     const size_t ctr = align_up(sizeof(DevCounters), 256) + (size_t)kGapLevels / 8;
     const size_t sync = align_up(sizeof(pog::BfsSync), 256);
     const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
-    const size_t tiles = align_up(sizeof(int32_t) * (size_t)pog::tile_count(g->grid_dims()), 256);
+    const size_t tiles = align_up(sizeof(int32_t) * (size_t)pog::tile_count(g->grid_dims(), g->tile_shape), 256);
     g->arena_bytes = per * (arrays + 2) + heights + ctr + sync + trace + 2 * tiles + 256;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {

@@ -23,7 +23,6 @@ namespace {
 
 constexpr int kBfsThreads = 256;
 constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1-2 s of polling at worst
-constexpr int kBottomUpRatio = 8;  // bottom-up once the frontier exceeds 1/8 of the unlabelled nodes
 
 // Sense-reversing grid barrier over co-resident blocks; false once the wait timed out.
 __device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err) {
@@ -73,7 +72,8 @@ __device__ __forceinline__ void decode(const Grid &g, int u, int &x, int &y, int
 }
 
 template <bool SOFT>
-__global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa, int *qb, BfsSync *sync) {
+__global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa, int *qb, BfsSync *sync,
+                                                                int bottom_up_ratio) {
     const unsigned nblocks = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa,
         __syncthreads();
         if (n == 0) break;
         unvisited -= n;
-        const bool bottom_up = (long long)n * kBottomUpRatio > unvisited;
+        const bool bottom_up = bottom_up_ratio > 0 && (long long)n * bottom_up_ratio > unvisited;
         if (tid == 0) {
             s->size[(level + 2) % 3] = 0;  // level-1's counter, free again
             if (g.trace && level <= kTraceLevels) {
@@ -215,9 +215,9 @@ __global__ void __launch_bounds__(kBfsThreads) k_cut_reach(Grid g, int *qa, int 
     if (tid == 0) g.ctr->max_label = level;
 }
 
+// Grid of a cooperative launch: `blocks_per_sm` (default 4) co-resident blocks per SM.
 template <class K>
-cudaError_t coop_launch(K kernel, const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
-                        cudaStream_t st) {
+cudaError_t coop_blocks(K kernel, int blocks_per_sm, int &blocks) {
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -226,25 +226,34 @@ cudaError_t coop_launch(K kernel, const Grid &g, int *qa, int *qb, BfsSync *sync
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBfsThreads, 0)) != cudaSuccess) return e;
     const int want = blocks_per_sm > 0 ? blocks_per_sm : 4;
-    const int blocks = sms * (per_sm < want ? per_sm : want);  // co-resident by construction
-    if (blocks < 1) return cudaErrorInvalidConfiguration;
+    blocks = sms * (per_sm < want ? per_sm : want);  // co-resident by construction
+    return blocks < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
+
+template <class K>
+cudaError_t coop_launch(K kernel, void **args, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
+    int blocks = 0;
+    cudaError_t e = coop_blocks(kernel, blocks_per_sm, blocks);
+    if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sync, 0, sizeof(BfsSync), st)) != cudaSuccess) return e;
-    Grid gg = g;
-    void *args[] = {&gg, &qa, &qb, &sync};
     return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(kernel), blocks, kBfsThreads, args, 0, st);
 }
 
 }  // namespace
 
 cudaError_t launch_global_relabel(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
-                                  cudaStream_t st) {
-    if (g.gs[0]) return coop_launch(k_global_relabel<true>, g, qa, qb, sync, blocks_per_sm, st);
-    return coop_launch(k_global_relabel<false>, g, qa, qb, sync, blocks_per_sm, st);
+                                  int bottom_up_ratio, cudaStream_t st) {
+    Grid gg = g;
+    void *args[] = {&gg, &qa, &qb, &sync, &bottom_up_ratio};
+    if (g.gs[0]) return coop_launch(k_global_relabel<true>, args, sync, blocks_per_sm, st);
+    return coop_launch(k_global_relabel<false>, args, sync, blocks_per_sm, st);
 }
 
 cudaError_t launch_cut_reach(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
-    if (g.gs[0]) return coop_launch(k_cut_reach<true>, g, qa, qb, sync, blocks_per_sm, st);
-    return coop_launch(k_cut_reach<false>, g, qa, qb, sync, blocks_per_sm, st);
+    Grid gg = g;
+    void *args[] = {&gg, &qa, &qb, &sync};
+    if (g.gs[0]) return coop_launch(k_cut_reach<true>, args, sync, blocks_per_sm, st);
+    return coop_launch(k_cut_reach<false>, args, sync, blocks_per_sm, st);
 }
 
 }  // namespace pog

@@ -211,6 +211,7 @@ struct pog_graph {
     long long flow;
     int sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks;
     float relabel_factor;
+    int tile_shape, bu_ratio;
     pog::Grid grid_dims() const {
         pog::Grid d{};
         d.X = X;

@@ -76,7 +76,7 @@ size_t scratch_bytes(int X, int Y, int Z, int alpha) {
     dims.X = X;
     dims.Y = Y;
     dims.Z = Z;
-    const size_t tiles = (size_t)pog::tile_count(dims);
+    const size_t tiles = (size_t)pog::tile_count_max(dims);
     return (arrays + 2) * align_up(N * 4, 256) + 2 * align_up(tiles * 4, 256) + 256 +
            align_up(sizeof(pog::BfsSync), 256) + align_up(sizeof(pog::DevCounters), 256) + kGapLevels / 8;
 }
@@ -126,7 +126,9 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     for (auto &s : g.gs) s = alpha > 0 ? c.take<int32_t>(N * 4) : nullptr;
     int32_t *queue_a = c.take<int32_t>(N * 4);
     int32_t *queue_b = c.take<int32_t>(N * 4);
-    const size_t tiles = (size_t)pog::tile_count(g);
+    const size_t tiles = (size_t)pog::tile_count_max(g);
+    const int shape = (opt && opt->tile_shape > 0 && opt->tile_shape < pog::kTileShapes) ? opt->tile_shape : 0;
+    const int bu_ratio = !opt || opt->bfs_bottom_up_ratio == 0 ? 8 : (opt->bfs_bottom_up_ratio < 0 ? 0 : opt->bfs_bottom_up_ratio);
     int32_t *tile_flag = c.take<int32_t>(tiles * 4);
     int32_t *tile_list = c.take<int32_t>(tiles * 4);
     int32_t *tile_work = c.take<int32_t>(256);
@@ -147,7 +149,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     const size_t active_off = offsetof(pog::DevCounters, active);
     for (int round = 0;; ++round) {
         NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + active_off, 0, sizeof(host.active), st));
-        NA_TRY_CUDA(pog::launch_global_relabel(g, queue_a, queue_b, sync, bfs_blocks, st));
+        NA_TRY_CUDA(pog::launch_global_relabel(g, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
         NA_TRY(read_counters(g, host, st));
         if (host.active == 0) break;
         if (round + 1 >= max_rounds) return POG_E_NOCONVERGE;
@@ -155,7 +157,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
             if (flags & POG_FLAG_NODE_SWEEPS)
                 NA_TRY_CUDA(pog::launch_sweep(g, queue_a, &sync->size[0], kNodeOps, st));
             else
-                NA_TRY_CUDA(pog::launch_tile_sweep(g, tile_flag, tile_list, tile_work, tile_sweeps, st));
+                NA_TRY_CUDA(pog::launch_tile_sweep(g, shape, tile_flag, tile_list, tile_work, tile_sweeps, st));
             if (!(flags & POG_FLAG_NO_GAP) && k + 1 == sweeps / 2) {
                 NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + offsetof(pog::DevCounters, max_label),
                                             0, sizeof(int), st));

@@ -20,21 +20,31 @@ namespace pog {
 
 namespace {
 
-constexpr int TX = 4, TY = 8, TZ = 32;
-constexpr int kCols = TX * TY;         // columns per tile
-constexpr int kTileNodes = kCols * TZ;  // 1024
+constexpr int kTileNodes = 1024;  // nodes per tile, every shape
 constexpr int kTileThreads = 256;
-constexpr int kPerThread = kTileNodes / kTileThreads;  // 4 nodes, one column each, same z
+constexpr int kPerThread = kTileNodes / kTileThreads;  // 4
+
+// Tile shapes (columns in x, columns in y, heights), all of 1024 nodes. Node s of a tile
+// sits at column c = s / TZ, height z0 + s % TZ, so consecutive threads read
+// consecutive heights of one column (coalesced along z).
+constexpr int kShapes[kTileShapes][3] = {{4, 8, 32}, {8, 8, 16}, {4, 4, 64}, {2, 4, 128}};
 
 struct TileGeom {
+    int tx, ty, tz;     // tile shape
     int ntx, nty, ntz;  // tiles per axis
 };
+
+TileGeom geom(const Grid &g, int shape) {
+    const int *sh = kShapes[shape];
+    return TileGeom{sh[0], sh[1], sh[2], (g.X + sh[0] - 1) / sh[0], (g.Y + sh[1] - 1) / sh[1],
+                    (g.Z + sh[2] - 1) / sh[2]};
+}
 
 __device__ __forceinline__ int tile_of(const Grid &g, const TileGeom &t, int u) {
     const int z = u % g.Z;
     const int col = u / g.Z;
     const int x = col / g.Y, y = col - x * g.Y;
-    return ((x / TX) * t.nty + (y / TY)) * t.ntz + z / TZ;
+    return ((x / t.tx) * t.nty + (y / t.ty)) * t.ntz + z / t.tz;
 }
 
 __global__ void __launch_bounds__(256) k_collect_tiles(Grid g, TileGeom t, int *flag, int *list, int *count) {
@@ -48,7 +58,7 @@ __global__ void __launch_bounds__(256) k_collect_tiles(Grid g, TileGeom t, int *
 }
 
 // Shared-memory image of a tile: current values and the values at load time (for the
-// delta write-back). Arrays are indexed by c * TZ + dz.
+// delta write-back). Arrays are indexed by the node's place s in the tile.
 struct TileSmem {
     int lab[kTileNodes], exc[kTileNodes], snk[kTileNodes], fdn[kTileNodes];
     int fh[4][kTileNodes];
@@ -66,7 +76,7 @@ struct Where {
     int gidx;  // global node index
 };
 
-template <bool SOFT>
+template <int TX, int TY, int TZ, bool SOFT>
 __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, TileGeom tg, const int *list,
                                                                     const int *count, int *flag, int *next,
                                                                     int local_sweeps) {
@@ -74,7 +84,6 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
     TileSoft &SS = *reinterpret_cast<TileSoft *>(reinterpret_cast<char *>(smem_raw) + sizeof(TileSmem));
     __shared__ int tile_id;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ntiles = *count;
     for (;;) {
         __syncthreads();
@@ -90,16 +99,16 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
         const int x0 = (txy / tg.nty) * TX, y0 = (txy % tg.nty) * TY, z0 = tz * TZ;
         if (threadIdx.x == 0) flag[tile] = 0;  // the tile may be listed again by a later scan
 
-        // ---- load (coalesced: a warp reads 32 consecutive heights of one column)
+        // ---- load (coalesced along z)
         int node[kPerThread];
         bool own[kPerThread];
 #pragma unroll
         for (int k = 0; k < kPerThread; ++k) {
-            const int c = warp + 8 * k;  // column within the tile
-            const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + lane;
+            const int s = threadIdx.x + kTileThreads * k;
+            const int c = s / TZ;  // column within the tile
+            const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
             own[k] = x < g.X && y < g.Y && z < g.Z && z >= 1;
             node[k] = own[k] ? (x * g.Y + y) * g.Z + z : -1;
-            const int s = c * TZ + lane;
             const int u = node[k];
             S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
             const int e = own[k] ? ldcg(g.exc + u) : 0;
@@ -146,9 +155,9 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
 #pragma unroll 1
             for (int k = 0; k < kPerThread; ++k) {
                 if (!own[k]) continue;
-                const int c = warp + 8 * k;
-                const int s = c * TZ + lane;
-                const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + lane;
+                const int s = threadIdx.x + kTileThreads * k;
+                const int c = s / TZ;
+                const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
                 const int e = vexc[s];
                 const int h = vlab[s];
                 if (e <= 0 || h >= POG_INF) continue;
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
 #pragma unroll
         for (int k = 0; k < kPerThread; ++k) {
             if (!own[k]) continue;
-            const int s = (warp + 8 * k) * TZ + lane;
+            const int s = threadIdx.x + kTileThreads * k;
             const int u = node[k];
             g.lab[u] = S.lab[s];
             g.snk[u] = S.snk[s];
@@ -283,34 +292,59 @@ int sm_count() {
 
 }  // namespace
 
-long long tile_count(const Grid &g) {
-    return (long long)((g.X + TX - 1) / TX) * ((g.Y + TY - 1) / TY) * ((g.Z + TZ - 1) / TZ);
+long long tile_count(const Grid &g, int shape) {
+    const TileGeom t = geom(g, shape < 0 || shape >= kTileShapes ? 0 : shape);
+    return (long long)t.ntx * t.nty * t.ntz;
+}
+
+long long tile_count_max(const Grid &g) {
+    long long m = 0;
+    for (int i = 0; i < kTileShapes; ++i) m = tile_count(g, i) > m ? tile_count(g, i) : m;
+    return m;
+}
+
+template <int TX, int TY, int TZ>
+cudaError_t launch_tile_kernel(const Grid &g, const TileGeom &t, int *flag, int *list, int *work, int local_sweeps,
+                               int blocks, cudaStream_t st) {
+    const bool soft = g.gs[0] != nullptr;
+    const size_t smem = sizeof(TileSmem) + (soft ? sizeof(TileSoft) : 0);
+    static bool configured[2] = {false, false};
+    cudaError_t e = cudaSuccess;
+    if (!configured[soft]) {
+        e = soft ? cudaFuncSetAttribute(k_tile_push_relabel<TX, TY, TZ, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_tile_push_relabel<TX, TY, TZ, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[soft] = true;
+    }
+    if (soft)
+        k_tile_push_relabel<TX, TY, TZ, true><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1,
+                                                                                 local_sweeps);
+    else
+        k_tile_push_relabel<TX, TY, TZ, false><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1,
+                                                                                  local_sweeps);
+    return cudaGetLastError();
 }
 
 // One tiled sweep: list the tiles that hold an active node, then let persistent blocks
 // take tiles from the list. `work` holds [count, next]; `flag` is one int per tile and
 // must start zeroed (each visited tile clears its own flag).
-cudaError_t launch_tile_sweep(const Grid &g, int *flag, int *list, int *work, int local_sweeps, cudaStream_t st) {
-    TileGeom t{(g.X + TX - 1) / TX, (g.Y + TY - 1) / TY, (g.Z + TZ - 1) / TZ};
+cudaError_t launch_tile_sweep(const Grid &g, int shape, int *flag, int *list, int *work, int local_sweeps,
+                              cudaStream_t st) {
+    if (shape < 0 || shape >= kTileShapes) shape = 0;
+    const TileGeom t = geom(g, shape);
     cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
     k_collect_tiles<<<sms * 8, 256, 0, st>>>(g, t, flag, list, work);
-    const bool soft = g.gs[0] != nullptr;
-    const size_t smem = sizeof(TileSmem) + (soft ? sizeof(TileSoft) : 0);
-    static bool configured[2] = {false, false};
-    if (!configured[soft]) {
-        e = soft ? cudaFuncSetAttribute(k_tile_push_relabel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                 : cudaFuncSetAttribute(k_tile_push_relabel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured[soft] = true;
-    }
     const int blocks = sms * 3;
-    if (soft)
-        k_tile_push_relabel<true><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1, local_sweeps);
-    else
-        k_tile_push_relabel<false><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1, local_sweeps);
-    return cudaGetLastError();
+    switch (shape) {
+        case 1: return launch_tile_kernel<8, 8, 16>(g, t, flag, list, work, local_sweeps, blocks, st);
+        case 2: return launch_tile_kernel<4, 4, 64>(g, t, flag, list, work, local_sweeps, blocks, st);
+        case 3: return launch_tile_kernel<2, 4, 128>(g, t, flag, list, work, local_sweeps, blocks, st);
+        default: return launch_tile_kernel<4, 8, 32>(g, t, flag, list, work, local_sweeps, blocks, st);
+    }
 }
 
 }  // namespace pog

@@ -43,7 +43,8 @@ class PogError(RuntimeError):
 class pog_options(ctypes.Structure):
     _fields_ = [("sweeps_per_relabel", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("tile_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32), ("bfs_blocks_per_sm", ctypes.c_int32),
-                ("relabel_factor", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
+                ("relabel_factor", ctypes.c_float), ("tile_shape", ctypes.c_int32),
+                ("bfs_bottom_up_ratio", ctypes.c_int32)]
 
 
 class pog_stats_t(ctypes.Structure):
@@ -125,8 +126,9 @@ def _dev(t, dtype, name):
 
 
 def make_options(sweeps_per_relabel=0, max_rounds=0, tile_sweeps=0, flags=0, bfs_blocks_per_sm=0,
-                 relabel_factor=0.0) -> pog_options:
-    return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks_per_sm, relabel_factor)
+                 relabel_factor=0.0, tile_shape=0, bfs_bottom_up_ratio=0) -> pog_options:
+    return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks_per_sm, relabel_factor,
+                       tile_shape, bfs_bottom_up_ratio)
 
 
 def pog_strerror(status: int) -> str:

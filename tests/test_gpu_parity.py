@@ -73,10 +73,12 @@ def test_delta_sweep(delta):
 
 @pytest.mark.parametrize("X,Y,Z,delta,alpha", [(37, 23, 50, 2, 5), (33, 65, 70, 3, 50), (70, 31, 41, 1, 0),
                                                 (64, 64, 96, 2, 0), (9, 17, 33, 0, 20), (5, 3, 130, 40, 3)])
-@pytest.mark.parametrize("mode", ["tiles", "nodes"])
+@pytest.mark.parametrize("mode", ["tiles", "nodes", "shape1", "shape3"])
 def test_ragged_horizon_volumes(X, Y, Z, delta, alpha, mode):
     cost = synth.horizon_cost(synth.scaled_spec(X, Y, Z, synth.BASE_SEED + X, stream=500 + Y))
-    assert_parity(cost, delta, alpha, **({"flags": pog.POG_FLAG_NODE_SWEEPS} if mode == "nodes" else {}))
+    opt = {"nodes": {"flags": pog.POG_FLAG_NODE_SWEEPS}, "shape1": {"tile_shape": 1},
+           "shape3": {"tile_shape": 3}}.get(mode, {})
+    assert_parity(cost, delta, alpha, **opt)
 
 
 def test_degenerate_volumes():
@@ -111,7 +113,9 @@ def test_options_do_not_change_results():
     ref = oracle.solve(cost, 2, 10)
     for opt in [dict(sweeps_per_relabel=1), dict(sweeps_per_relabel=64, tile_sweeps=1),
                 dict(flags=pog.POG_FLAG_NO_GAP), dict(tile_sweeps=16), dict(flags=pog.POG_FLAG_NODE_SWEEPS),
-                dict(flags=pog.POG_FLAG_NO_PREPUSH), dict(bfs_blocks_per_sm=1), dict(tile_sweeps=64)]:
+                dict(flags=pog.POG_FLAG_NO_PREPUSH), dict(bfs_blocks_per_sm=1), dict(tile_sweeps=64),
+                dict(tile_shape=1), dict(tile_shape=2), dict(tile_shape=3), dict(bfs_bottom_up_ratio=-1),
+                dict(bfs_bottom_up_ratio=1), dict(relabel_factor=0.25), dict(sweeps_per_relabel=3, tile_shape=3)]:
         flow, h = gpu_solve(cost, 2, 10, **opt)
         assert flow == ref.flow
         np.testing.assert_array_equal(h, ref.heights)
