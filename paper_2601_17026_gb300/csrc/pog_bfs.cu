@@ -54,6 +54,27 @@ __device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err
     return ok;
 }
 
+// Append up to kMaxArcs nodes per lane (slot k of `hd.node` when bit k of `mask`) with
+// one atomic per warp; every lane of the warp must call it.
+__device__ __forceinline__ void warp_append_mask(unsigned mask, const Hood &hd, int *queue, int *size) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    int base = 0;
+    if (lane == 31) base = atomicAdd(size, total);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k)
+        if (mask & (1u << k)) queue[base++] = hd.node[k];
+}
+
 // Append `u` to a queue; the lanes that append together share one atomic.
 __device__ __forceinline__ void warp_append(int u, int *queue, int *size) {
     namespace cg = cooperative_groups;
@@ -118,7 +139,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa,
                 decode(g, u, x, y, z);
                 if (z == 0) continue;
                 Hood hd;
-                gather_out<SOFT>(g, u, x, y, z, hd);
+                gather_out<SOFT, true>(g, u, x, y, z, hd);
                 bool hit = false;
 #pragma unroll
                 for (int k = 0; k < kMaxArcs; ++k) hit |= hd.lab[k] == level;
@@ -128,21 +149,28 @@ __global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa,
                 }
             }
         } else {
-            // top-down: expand the frontier queue along residual arcs into its nodes
+            // top-down: expand the frontier queue along residual arcs into its nodes; all
+            // claims of a thread are issued together, appends cost one atomic per warp
             for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
                 const int i = base + threadIdx.x;
+                unsigned won = 0;
+                Hood hd;
                 if (i < n) {
                     const int v = cur[i];
                     int x, y, z;
                     decode(g, v, x, y, z);
-                    Hood hd;
-                    gather_in<SOFT>(g, v, x, y, z, hd);
+                    gather_in<SOFT, true>(g, v, x, y, z, hd);
+                    int old[kMaxArcs];
 #pragma unroll
                     for (int k = 0; k < kMaxArcs; ++k)
-                        if (hd.res[k] > 0 && hd.lab[k] == POG_INF &&
-                            atomicCAS(g.lab + hd.node[k], POG_INF, level + 1) == POG_INF)
-                            warp_append(hd.node[k], nxt, &s->size[(level + 1) % 3]);
+                        old[k] = (hd.res[k] > 0 && hd.lab[k] == POG_INF)
+                                     ? atomicCAS(g.lab + hd.node[k], POG_INF, level + 1)
+                                     : 0;
+#pragma unroll
+                    for (int k = 0; k < kMaxArcs; ++k)
+                        if (hd.res[k] > 0 && hd.lab[k] == POG_INF && old[k] == POG_INF) won |= 1u << k;
                 }
+                warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
             }
         }
         if (!grid_sync(s, nblocks, err)) return;
@@ -194,17 +222,22 @@ __global__ void __launch_bounds__(kBfsThreads) k_cut_reach(Grid g, int *qa, int 
         if (tid == 0) s->size[(level + 2) % 3] = 0;
         for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
             const int i = base + threadIdx.x;
+            unsigned won = 0;
+            Hood hd;
             if (i < n) {
                 const int u = cur[i];
                 int x, y, z;
                 decode(g, u, x, y, z);
-                Hood hd;
-                gather_out<SOFT>(g, u, x, y, z, hd);
+                gather_out<SOFT, true>(g, u, x, y, z, hd);
+                int old[kMaxArcs];
 #pragma unroll
                 for (int k = 0; k < kMaxArcs; ++k)
-                    if (hd.res[k] > 0 && hd.lab[k] == 0 && atomicCAS(g.lab + hd.node[k], 0, 1) == 0)
-                        warp_append(hd.node[k], nxt, &s->size[(level + 1) % 3]);
+                    old[k] = (hd.res[k] > 0 && hd.lab[k] == 0) ? atomicCAS(g.lab + hd.node[k], 0, 1) : 1;
+#pragma unroll
+                for (int k = 0; k < kMaxArcs; ++k)
+                    if (hd.res[k] > 0 && hd.lab[k] == 0 && old[k] == 0) won |= 1u << k;
             }
+            warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
         }
         if (!grid_sync(s, nblocks, err)) return;
         int *t = cur;

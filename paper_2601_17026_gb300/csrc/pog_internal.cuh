@@ -101,8 +101,15 @@ struct Hood {
     int lab[kMaxArcs];   // label (or mark) of the far end, POG_INF for an absent arc
 };
 
+// Loads of arc words: through L2 only while other threads may change them (sweeps), or
+// through the read-only path when they are constant for the kernel (relabel, cut).
+template <bool RO>
+__device__ __forceinline__ int ld_arc(const int32_t *p) {
+    return RO ? __ldg(p) : __ldcg(p);
+}
+
 // Out-arcs of u: slot 0 down, 1 up, 2+3d hard out, 3+3d hard in (reverse), 4+3d soft.
-template <bool SOFT>
+template <bool SOFT, bool RO = false>
 __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, int z, Hood &h) {
 #pragma unroll
     for (int i = 0; i < kMaxArcs; ++i) {
@@ -111,11 +118,11 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
     }
     if (z >= 2) {
         h.node[0] = u - 1;
-        h.res[0] = POG_CAP_INF - ldcg(g.fdn + u);
+        h.res[0] = POG_CAP_INF - ld_arc<RO>(g.fdn + u);
     }
     if (z + 1 < g.Z) {
         h.node[1] = u + 1;
-        h.res[1] = ldcg(g.fdn + u + 1);
+        h.res[1] = ld_arc<RO>(g.fdn + u + 1);
     }
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
@@ -124,17 +131,17 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
         if (!ok) continue;
         if (z - g.delta >= 1) {
             h.node[2 + 3 * d] = u + off - g.delta;
-            h.res[2 + 3 * d] = POG_CAP_INF - ldcg(g.fh[d] + u);
+            h.res[2 + 3 * d] = POG_CAP_INF - ld_arc<RO>(g.fh[d] + u);
         }
         if (z + g.delta < g.Z) {
             const int v = u + off + g.delta;
             h.node[3 + 3 * d] = v;
-            h.res[3 + 3 * d] = ldcg(g.fh[d ^ 1] + v);
+            h.res[3 + 3 * d] = ld_arc<RO>(g.fh[d ^ 1] + v);
         }
         if (SOFT) {
             const int v = u + off;
             h.node[4 + 3 * d] = v;
-            h.res[4 + 3 * d] = (d & 1) ? g.alpha - ldcg(g.gs[d >> 1] + u) : g.alpha + ldcg(g.gs[d >> 1] + v);
+            h.res[4 + 3 * d] = (d & 1) ? g.alpha - ld_arc<RO>(g.gs[d >> 1] + u) : g.alpha + ld_arc<RO>(g.gs[d >> 1] + v);
         }
     }
 #pragma unroll
@@ -146,7 +153,7 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
 
 // In-arcs of v (arcs u -> v): slot 0 from above, 1 from below, 2+3d hard arc of
 // (q, z+D), 3+3d reverse of v's hard arc, 4+3d soft.
-template <bool SOFT>
+template <bool SOFT, bool RO = false>
 __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, int z, Hood &h) {
 #pragma unroll
     for (int i = 0; i < kMaxArcs; ++i) {
@@ -155,11 +162,11 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
     }
     if (z + 1 < g.Z) {
         h.node[0] = v + 1;
-        h.res[0] = POG_CAP_INF - ldcg(g.fdn + v + 1);
+        h.res[0] = POG_CAP_INF - ld_arc<RO>(g.fdn + v + 1);
     }
     if (z >= 2) {
         h.node[1] = v - 1;
-        h.res[1] = ldcg(g.fdn + v);
+        h.res[1] = ld_arc<RO>(g.fdn + v);
     }
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
@@ -169,16 +176,16 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
         if (z + g.delta < g.Z) {
             const int u = v + off + g.delta;
             h.node[2 + 3 * d] = u;
-            h.res[2 + 3 * d] = POG_CAP_INF - ldcg(g.fh[d ^ 1] + u);
+            h.res[2 + 3 * d] = POG_CAP_INF - ld_arc<RO>(g.fh[d ^ 1] + u);
         }
         if (z - g.delta >= 1) {
             h.node[3 + 3 * d] = v + off - g.delta;
-            h.res[3 + 3 * d] = ldcg(g.fh[d] + v);
+            h.res[3 + 3 * d] = ld_arc<RO>(g.fh[d] + v);
         }
         if (SOFT) {
             const int u = v + off;
             h.node[4 + 3 * d] = u;
-            h.res[4 + 3 * d] = (d & 1) ? g.alpha + ldcg(g.gs[d >> 1] + v) : g.alpha - ldcg(g.gs[d >> 1] + u);
+            h.res[4 + 3 * d] = (d & 1) ? g.alpha + ld_arc<RO>(g.gs[d >> 1] + v) : g.alpha - ld_arc<RO>(g.gs[d >> 1] + u);
         }
     }
 #pragma unroll

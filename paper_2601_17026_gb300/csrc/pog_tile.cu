@@ -57,6 +57,37 @@ __global__ void __launch_bounds__(256) k_collect_tiles(Grid g, TileGeom t, int *
     }
 }
 
+// Far end of arc slot k of node (x, y, z) (slots as in gather_out: 0 down, 1 up, then per
+// direction d: 2+3d hard out, 3+3d reverse of the neighbour's hard arc, 4+3d soft);
+// false when the arc does not exist.
+template <bool SOFT>
+__device__ __forceinline__ bool far_node(const Grid &g, int k, int x, int y, int z, int &x2, int &y2, int &z2) {
+    x2 = x;
+    y2 = y;
+    if (k == 0) {
+        z2 = z - 1;
+        return z >= 2;
+    }
+    if (k == 1) {
+        z2 = z + 1;
+        return z + 1 < g.Z;
+    }
+    const int d = (k - 2) / 3, kind = (k - 2) % 3;
+    x2 = x + (d == 0 ? -1 : d == 1 ? 1 : 0);
+    y2 = y + (d == 2 ? -1 : d == 3 ? 1 : 0);
+    if (x2 < 0 || x2 >= g.X || y2 < 0 || y2 >= g.Y) return false;
+    if (kind == 0) {
+        z2 = z - g.delta;
+        return z2 >= 1;
+    }
+    if (kind == 1) {
+        z2 = z + g.delta;
+        return z2 < g.Z;
+    }
+    z2 = z;
+    return SOFT;
+}
+
 // Shared-memory image of a tile: current values and the values at load time (for the
 // delta write-back). Arrays are indexed by the node's place s in the tile.
 struct TileSmem {
@@ -143,7 +174,6 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
             w.s = ((x - x0) * TY + (y - y0)) * TZ + (z - z0);
             return w;
         };
-        auto lab_of = [&](const Where &w) { return w.in ? ((volatile int *)S.lab)[w.s] : ldcg(g.lab + w.gidx); };
 
         // ---- local sweeps. Warps run them without block barriers (shared atomics keep
         // the tile consistent, and volatile reads see other warps' progress); a warp stops
@@ -173,64 +203,53 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
                     }
                     continue;
                 }
-                // gather: residual and far-end label of every arc (see gather_out)
-                int best = POG_INF, bk = -1, bres = 0, bd = 0;
-                Where bw;
-                bw.in = false;
-                bw.s = 0;
-                bw.gidx = 0;
-                auto consider = [&](int kind, int dir, const Where &w, int res) {
-                    if (res <= 0) return;
-                    const int l = lab_of(w);
-                    if (l < best) {
-                        best = l;
-                        bk = kind;
-                        bd = dir;
-                        bw = w;
-                        bres = res;
-                    }
-                };
-                volatile int *vfdn = S.fdn;
-                if (z >= 2) consider(ARC_DOWN, 0, where(x, y, z - 1), POG_CAP_INF - vfdn[s]);
-                if (z + 1 < g.Z) {
-                    const Where w = where(x, y, z + 1);
-                    consider(ARC_UP, 0, w, w.in ? vfdn[w.s] : ldcg(g.fdn + w.gidx));
-                }
+                // gather: residual and far-end label of every arc (slots as in gather_out),
+                // every load issued before any is used
+                int res[kMaxArcs], far_lab[kMaxArcs];
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    const int xq = x + (d == 0 ? -1 : d == 1 ? 1 : 0);
-                    const int yq = y + (d == 2 ? -1 : d == 3 ? 1 : 0);
-                    if (xq < 0 || xq >= g.X || yq < 0 || yq >= g.Y) continue;
-                    volatile int *vfh = S.fh[d];
-                    volatile int *vfho = S.fh[d ^ 1];
-                    if (z - g.delta >= 1) consider(ARC_HOUT, d, where(xq, yq, z - g.delta), POG_CAP_INF - vfh[s]);
-                    if (z + g.delta < g.Z) {
-                        const Where w = where(xq, yq, z + g.delta);
-                        consider(ARC_HIN, d, w, w.in ? vfho[w.s] : ldcg(g.fh[d ^ 1] + w.gidx));
-                    }
-                    if (SOFT) {
-                        volatile int *vgs = SS.gs[d >> 1];
-                        const Where w = where(xq, yq, z);
-                        int r;
-                        if (d & 1) r = g.alpha - vgs[s];
-                        else r = g.alpha + (w.in ? vgs[w.s] : ldcg(g.gs[d >> 1] + w.gidx));
-                        consider(ARC_SOFT, d, w, r);
-                    }
+                for (int k = 0; k < kMaxArcs; ++k) {
+                    int x2, y2, z2;
+                    res[k] = 0;
+                    far_lab[k] = POG_INF;
+                    if (!far_node<SOFT>(g, k, x, y, z, x2, y2, z2)) continue;
+                    const Where w = where(x2, y2, z2);
+                    const int d = k >= 2 ? (k - 2) / 3 : 0;
+                    const int kind = k < 2 ? k : 2 + (k - 2) % 3;  // 0 down, 1 up, 2 hout, 3 hin, 4 soft
+                    if (kind == 0) res[k] = POG_CAP_INF - ((volatile int *)S.fdn)[s];
+                    else if (kind == 1) res[k] = w.in ? ((volatile int *)S.fdn)[w.s] : ldcg(g.fdn + w.gidx);
+                    else if (kind == 2) res[k] = POG_CAP_INF - ((volatile int *)S.fh[d])[s];
+                    else if (kind == 3) res[k] = w.in ? ((volatile int *)S.fh[d ^ 1])[w.s] : ldcg(g.fh[d ^ 1] + w.gidx);
+                    else if (d & 1) res[k] = g.alpha - ((volatile int *)SS.gs[d >> 1])[s];
+                    else res[k] = g.alpha + (w.in ? ((volatile int *)SS.gs[d >> 1])[w.s] : ldcg(g.gs[d >> 1] + w.gidx));
+                    far_lab[k] = w.in ? vlab[w.s] : ldcg(g.lab + w.gidx);
                 }
-                if (bk < 0 || h <= best) {
+                int best = POG_INF, bk = -1, bres = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxArcs; ++k)
+                    if (res[k] > 0 && far_lab[k] < best) {
+                        best = far_lab[k];
+                        bk = k;
+                        bres = res[k];
+                    }
+                if (bk < 0 || h <= best) {  // relabel (Algorithm 2)
                     S.lab[s] = best >= POG_INF - 1 ? POG_INF : best + 1;
                     continue;
                 }
+                int x2, y2, z2;
+                far_node<SOFT>(g, bk, x, y, z, x2, y2, z2);
+                const Where bw = where(x2, y2, z2);
+                const int bd = bk >= 2 ? (bk - 2) / 3 : 0;
+                const int bkind = bk < 2 ? bk : 2 + (bk - 2) % 3;
                 const int delta = e < bres ? e : bres;
                 int sat = 0;
-                switch (bk) {
-                    case ARC_DOWN: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
-                    case ARC_UP:
+                switch (bkind) {
+                    case 0: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
+                    case 1:
                         if (bw.in) atomicSub(&S.fdn[bw.s], delta);
                         else atomicSub(g.fdn + bw.gidx, delta);
                         break;
-                    case ARC_HOUT: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
-                    case ARC_HIN:
+                    case 2: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
+                    case 3:
                         if (bw.in) atomicSub(&S.fh[bd ^ 1][bw.s], delta);
                         else atomicSub(g.fh[bd ^ 1] + bw.gidx, delta);
                         break;
