@@ -1,6 +1,8 @@
 // C ABI of the GB300 min-cut solver (declared in include/pog.h) and its host driver:
 // state allocation, the push/relabel <-> global-relabel iteration with its exact
-// termination test (Section 3.2.4), cut extraction and the flow value.
+// termination test (Section 3.2.4), cut extraction and the flow value. Every graph is a
+// batch: one volume for pog_build, several for pog_solve_batch, solved as the disjoint
+// union of their graphs by the same launches.
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
@@ -61,13 +63,20 @@ pog_status reset_field(pog_graph *g, T DevCounters::*field) {
     return from_cuda(cudaMemsetAsync((char *)g->ctr + off, 0, sizeof(T), g->stream));
 }
 
+// Union counters and every volume's counters to the pinned mirror, then the error words.
 pog_status read_counters(pog_graph *g) {
     POG_TRY_CUDA(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, g->stream));
+    POG_TRY_CUDA(cudaMemcpyAsync(g->ctr_host + 1, g->vctr, sizeof(DevCounters) * g->nvol, cudaMemcpyDeviceToHost,
+                                 g->stream));
     POG_TRY_CUDA(cudaStreamSynchronize(g->stream));
-    if (g->ctr_host->error & POG_ERR_TIMEOUT) return POG_E_TIMEOUT;
-    if (g->ctr_host->error) return POG_E_OVERFLOW;
+    int err = 0;
+    for (int v = 0; v <= g->nvol; ++v) err |= g->ctr_host[v].error;
+    if (err & POG_ERR_TIMEOUT) return POG_E_TIMEOUT;
+    if (err) return POG_E_OVERFLOW;
     return POG_OK;
 }
+
+const DevCounters &volume_counters(const pog_graph *g, int v) { return g->ctr_host[1 + v]; }
 
 enum { ST_BFS = 2, ST_CUT = 3, ST_SWEEP = 1, ST_ROUNDS = 0, ST_GAPS = 4, ST_ACTIVE0 = 5, ST_LAUNCHES = 6 };
 enum { TM_SWEEP = 0, TM_BFS = 1, TM_CUT = 2, TM_BUILD = 3 };
@@ -110,13 +119,13 @@ void fold_timers(pog_graph *g) {
     }
 }
 
-// Global relabel (exact reverse BFS from t, one cooperative launch) fused with the
-// termination count; returns the number of active nodes.
+// Global relabel (exact reverse BFS from t, one cooperative launch for the whole batch)
+// fused with the termination count; returns the number of active nodes.
 pog_status global_relabel(pog_graph *g, long long &active) {
     POG_TRY(reset_field(g, &DevCounters::active));
     POG_TRY_CUDA(cudaEventRecord(g->round_ev[0], g->stream));
     POG_TRY_CUDA(timed(g, TM_BFS, [&] {
-        return pog::launch_global_relabel(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->bu_ratio,
+        return pog::launch_global_relabel(g->batch, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->bu_ratio,
                                           g->stream);
     }));
     POG_TRY_CUDA(cudaEventRecord(g->round_ev[1], g->stream));
@@ -128,18 +137,19 @@ pog_status global_relabel(pog_graph *g, long long &active) {
 }
 
 unsigned int *gap_bits(pog_graph *g) {
-    // The bitmap sits after the counters in the arena.
+    // The bitmap sits after the union counters in the arena.
     return reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(g->ctr) + align_up(sizeof(DevCounters), 256));
 }
 
-pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
+pog_status maxflow_impl(pog_graph *g) {
     std::memset(g->stats, 0, sizeof g->stats);
+    g->stats[ST_LAUNCHES] = 2 * g->nvol;  // the builds
     for (int f = TM_SWEEP; f <= TM_CUT; ++f) g->timers[f].ms = 0.0;
     POG_TRY(read_counters(g));  // surfaces build errors (cost range)
     long long active = 0;
     if (!(g->flags & POG_FLAG_NO_PREPUSH)) {
-        POG_TRY_CUDA(pog::launch_column_prepush(g->grid, g->stream));
-        g->stats[ST_LAUNCHES] += 1;
+        for (int v = 0; v < g->nvol; ++v) POG_TRY_CUDA(pog::launch_column_prepush(g->vols[v], g->stream));
+        g->stats[ST_LAUNCHES] += g->nvol;
     }
     POG_TRY(global_relabel(g, active));
     g->stats[ST_ROUNDS] = 1;
@@ -158,14 +168,14 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
         for (int k = 0; k < sweeps; ++k) {
             POG_TRY_CUDA(timed(g, TM_SWEEP, [&] {
                 if (g->flags & POG_FLAG_NODE_SWEEPS)
-                    return pog::launch_sweep(g->grid, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
-                return pog::launch_tile_sweep(g->grid, g->tile_shape, g->tile_flag, g->tile_list, g->tile_work,
-                                              g->tile_sweeps, g->stream);
+                    return pog::launch_sweep(g->batch, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
+                return pog::launch_tile_sweep(g->batch, g->any_soft, g->tile_shape, g->tile_flag, g->tile_list,
+                                              g->tile_work, g->tile_sweeps, g->stream);
             }));
             if (gap && k + 1 == half) {
                 POG_TRY(reset_field(g, &DevCounters::raised));
                 POG_TRY(reset_field(g, &DevCounters::max_label));
-                POG_TRY_CUDA(pog::launch_gap(g->grid, gap_bits(g), kGapLevels, g->stream));
+                POG_TRY_CUDA(pog::launch_gap(g->batch, gap_bits(g), kGapLevels, g->stream));
                 g->stats[ST_LAUNCHES] += 3;
                 g->stats[ST_GAPS]++;
             }
@@ -184,58 +194,108 @@ pog_status maxflow_impl(pog_graph *g, int64_t *flow_out) {
             sweeps = (int)want;
         }
     }
-    // Maximum preflow reached: extract the minimal cut, the heights and the flow value.
+    // Maximum preflow reached: extract the minimal cut, the heights and the flow values.
     POG_TRY_CUDA(timed(g, TM_CUT, [&] {
-        return pog::launch_cut_reach(g->grid, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
+        return pog::launch_cut_reach(g->batch, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
     }));
-    g->stats[ST_LAUNCHES] += 5;  // cut, heights, excess sum, and the build's two kernels
-    POG_TRY_CUDA(pog::launch_heights(g->grid, g->heights, g->stream));
-    POG_TRY(reset_field(g, &DevCounters::excess_sum));
-    POG_TRY_CUDA(pog::launch_excess_sum(g->grid, g->stream));
+    for (int v = 0; v < g->nvol; ++v) {
+        POG_TRY_CUDA(pog::launch_heights(g->vols[v], g->heights + g->col_base[v], g->stream));
+        POG_TRY_CUDA(cudaMemsetAsync(&g->vctr[v].excess_sum, 0, sizeof(unsigned long long), g->stream));
+        POG_TRY_CUDA(pog::launch_excess_sum(g->vols[v], g->stream));
+    }
+    g->stats[ST_LAUNCHES] += 1 + 2 * g->nvol;  // cut, heights and excess sums
     POG_TRY(read_counters(g));
     g->stats[ST_CUT] = g->ctr_host->max_label;  // BFS levels of the cut extraction
-    const DevCounters &c = *g->ctr_host;
-    g->flow = (long long)c.bottom_const + (long long)c.src_total - (long long)c.excess_sum;
+    for (int v = 0; v < g->nvol; ++v) {
+        const DevCounters &c = volume_counters(g, v);
+        g->flows[v] = (long long)c.bottom_const + (long long)c.src_total - (long long)c.excess_sum;
+    }
+    g->flow = g->flows[0];
     fold_timers(g);
     g->solved = 1;
-    *flow_out = g->flow;
     return POG_OK;
 }
 
+struct VolumeSpec {
+    int X, Y, Z, delta, alpha;
+};
+
+bool valid_volume(const VolumeSpec &v) {
+    return v.X >= 1 && v.Y >= 1 && v.Z >= 1 && v.delta >= 0 && v.alpha >= 0 && v.alpha < (1 << 30);
+}
+
+// Allocate a batch graph for `n` volumes and lay out its arena; `launch(v, grid, stream)`
+// enqueues the build of volume v.
 template <class Launch>
-pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha, const pog_options *opt,
-                      void *stream, pog_graph **out, Launch launch) {
-    if (!out || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 || alpha >= (1 << 30)) return POG_E_INVALID;
-    const long long N = (long long)X * Y * Z;
-    if (N >= (1ll << 31) - 64) return POG_E_INVALID;
+pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, void *stream, pog_graph **out,
+                       Launch launch) {
+    if (!out || n < 1 || n > pog::kMaxVolumes) return POG_E_INVALID;
+    long long total = 0, soft_total = 0, cols = 0;
+    for (int v = 0; v < n; ++v) {
+        if (!valid_volume(spec[v])) return POG_E_INVALID;
+        const long long N = (long long)spec[v].X * spec[v].Y * spec[v].Z;
+        total += N;
+        if (spec[v].alpha > 0) soft_total += N;
+        cols += (long long)spec[v].X * spec[v].Y;
+    }
+    if (total >= (1ll << 31) - 64) return POG_E_INVALID;
     pog_graph *g = new (std::nothrow) pog_graph();
     if (!g) return POG_E_NOMEM;
-    g->X = X;
-    g->Y = Y;
-    g->Z = Z;
-    g->delta = delta;
-    g->alpha = alpha;
-    g->N = N;
+    g->nvol = n;
+    g->X = spec[0].X;
+    g->Y = spec[0].Y;
+    g->Z = spec[0].Z;
+    g->delta = spec[0].delta;
+    g->alpha = spec[0].alpha;
+    g->N = (long long)g->X * g->Y * g->Z;
+    g->n_total = total;
+    g->any_soft = soft_total > 0;
     g->stream = static_cast<cudaStream_t>(stream);
     set_options(g, opt);
-    const int arrays = alpha > 0 ? 10 : 8;
-    const size_t per = align_up((size_t)N * sizeof(int32_t), 256);
-    const size_t heights = align_up((size_t)X * Y * sizeof(int32_t), 256);
+    g->vols = new (std::nothrow) Grid[n]();
+    g->node_base = new (std::nothrow) int[n + 1];
+    g->tile_base = new (std::nothrow) int[n + 1];
+    g->col_base = new (std::nothrow) long long[n + 1];
+    g->flows = new (std::nothrow) long long[n]();
+    if (!g->vols || !g->node_base || !g->tile_base || !g->col_base || !g->flows) {
+        pog_free(g);
+        return POG_E_NOMEM;
+    }
+    long long tiles = 0;
+    g->node_base[0] = 0;
+    g->tile_base[0] = 0;
+    g->col_base[0] = 0;
+    for (int v = 0; v < n; ++v) {
+        Grid d{};
+        d.X = spec[v].X;
+        d.Y = spec[v].Y;
+        d.Z = spec[v].Z;
+        tiles += pog::tile_count(d, g->tile_shape);
+        g->node_base[v + 1] = g->node_base[v] + spec[v].X * spec[v].Y * spec[v].Z;
+        g->tile_base[v + 1] = (int)tiles;
+        g->col_base[v + 1] = g->col_base[v] + (long long)spec[v].X * spec[v].Y;
+    }
+    const size_t per = align_up((size_t)total * sizeof(int32_t), 256);
+    const size_t per_soft = align_up((size_t)soft_total * sizeof(int32_t), 256);
+    const size_t heights = align_up((size_t)cols * sizeof(int32_t), 256);
     const size_t ctr = align_up(sizeof(DevCounters), 256) + (size_t)kGapLevels / 8;
+    const size_t vctr = align_up(sizeof(DevCounters) * n, 256);
     const size_t sync = align_up(sizeof(pog::BfsSync), 256);
     const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
-    const size_t tiles = align_up(sizeof(int32_t) * (size_t)pog::tile_count(g->grid_dims(), g->tile_shape), 256);
-    g->arena_bytes = per * (arrays + 2) + heights + ctr + sync + trace + 2 * tiles + 256;
+    const size_t tile_bytes = align_up(sizeof(int32_t) * (size_t)tiles, 256);
+    const size_t table = align_up(sizeof(Grid) * n, 256) + 2 * align_up(sizeof(int) * (n + 1), 256);
+    g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 2 * tile_bytes + 256 + table;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        delete g;
+        g->arena = nullptr;
+        pog_free(g);
         return e == cudaErrorMemoryAllocation ? POG_E_NOMEM : POG_E_CUDA;
     }
-    e = cudaHostAlloc(reinterpret_cast<void **>(&g->ctr_host), sizeof(DevCounters), cudaHostAllocDefault);
+    e = cudaHostAlloc(reinterpret_cast<void **>(&g->ctr_host), sizeof(DevCounters) * (n + 1), cudaHostAllocDefault);
     if (e != cudaSuccess) {
-        cudaFree(g->arena);
-        delete g;
+        g->ctr_host = nullptr;
+        pog_free(g);
         return POG_E_NOMEM;
     }
     for (auto &ev : g->round_ev) {
@@ -245,48 +305,81 @@ pog_status build_impl(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t al
             return POG_E_CUDA;
         }
     }
+    // ---- arena layout
     char *p = static_cast<char *>(g->arena);
-    Grid &gr = g->grid;
-    gr.X = X;
-    gr.Y = Y;
-    gr.Z = Z;
-    gr.delta = delta;
-    gr.alpha = alpha;
-    gr.N = (int)N;
-    int32_t **slots[10] = {&gr.lab, &gr.exc, &gr.snk, &gr.fdn, &gr.fh[0], &gr.fh[1], &gr.fh[2], &gr.fh[3],
-                           &gr.gs[0], &gr.gs[1]};
-    for (int i = 0; i < 10; ++i) {
-        *slots[i] = i < arrays ? reinterpret_cast<int32_t *>(p) : nullptr;
-        if (i < arrays) p += per;
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += bytes;
+        return r;
+    };
+    int32_t *arr[8];
+    for (auto &a : arr) a = reinterpret_cast<int32_t *>(take(per));
+    int32_t *soft[2];
+    for (auto &a : soft) a = reinterpret_cast<int32_t *>(take(per_soft));
+    g->queue_a = reinterpret_cast<int32_t *>(take(per));
+    g->queue_b = reinterpret_cast<int32_t *>(take(per));
+    g->heights = reinterpret_cast<int32_t *>(take(heights));
+    g->bfs_sync = reinterpret_cast<pog::BfsSync *>(take(sync));
+    g->trace = reinterpret_cast<pog::LevelTrace *>(take(trace));
+    g->tile_flag = reinterpret_cast<int32_t *>(take(tile_bytes));
+    g->tile_list = reinterpret_cast<int32_t *>(take(tile_bytes));
+    g->tile_work = reinterpret_cast<int32_t *>(take(256));
+    g->vctr = reinterpret_cast<DevCounters *>(take(vctr));
+    g->vols_dev = reinterpret_cast<Grid *>(take(align_up(sizeof(Grid) * n, 256)));
+    g->node_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
+    g->tile_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
+    g->ctr = reinterpret_cast<DevCounters *>(take(ctr));
+    long long soft_off = 0;
+    for (int v = 0; v < n; ++v) {
+        Grid &gr = g->vols[v];
+        const long long off = g->node_base[v];
+        gr.X = spec[v].X;
+        gr.Y = spec[v].Y;
+        gr.Z = spec[v].Z;
+        gr.delta = spec[v].delta;
+        gr.alpha = spec[v].alpha;
+        gr.N = g->node_base[v + 1] - g->node_base[v];
+        gr.lab = arr[0] + off;
+        gr.exc = arr[1] + off;
+        gr.snk = arr[2] + off;
+        gr.fdn = arr[3] + off;
+        for (int d = 0; d < 4; ++d) gr.fh[d] = arr[4 + d] + off;
+        for (int k = 0; k < 2; ++k) gr.gs[k] = spec[v].alpha > 0 ? soft[k] + soft_off : nullptr;
+        if (spec[v].alpha > 0) soft_off += gr.N;
+        gr.ctr = g->vctr + v;
+        gr.trace = nullptr;
     }
-    g->queue_a = reinterpret_cast<int32_t *>(p);
-    p += per;
-    g->queue_b = reinterpret_cast<int32_t *>(p);
-    p += per;
-    g->heights = reinterpret_cast<int32_t *>(p);
-    p += heights;
-    g->bfs_sync = reinterpret_cast<pog::BfsSync *>(p);
-    p += sync;
-    g->trace = reinterpret_cast<pog::LevelTrace *>(p);
-    p += trace;
-    gr.trace = g->trace;
-    g->tile_flag = reinterpret_cast<int32_t *>(p);
-    p += tiles;
-    g->tile_list = reinterpret_cast<int32_t *>(p);
-    p += tiles;
-    g->tile_work = reinterpret_cast<int32_t *>(p);
-    p += 256;
-    g->ctr = reinterpret_cast<DevCounters *>(p);
-    gr.ctr = g->ctr;
-    e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_flag, 0, tiles, g->stream);
-    if (e == cudaSuccess) e = timed(g, TM_BUILD, [&] { return launch(gr, g->stream); });
+    g->grid = g->vols[0];
+    g->batch.vols = g->vols_dev;
+    g->batch.node_base = g->node_base_dev;
+    g->batch.tile_base = g->tile_base_dev;
+    g->batch.nvol = n;
+    g->batch.n_total = (int)total;
+    g->batch.ctr = g->ctr;
+    g->batch.trace = g->trace;
+    e = cudaMemcpyAsync(g->vols_dev, g->vols, sizeof(Grid) * n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->node_base_dev, g->node_base, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->tile_base_dev, g->tile_base, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->vctr, 0, sizeof(DevCounters) * n, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_flag, 0, tile_bytes, g->stream);
+    for (int v = 0; v < n && e == cudaSuccess; ++v)
+        e = timed(g, TM_BUILD, [&] { return launch(v, g->vols[v], g->stream); });
     if (e != cudaSuccess) {
         pog_free(g);
         return from_cuda(e);
     }
     *out = g;
     return POG_OK;
+}
+
+template <class Launch>
+pog_status build_one(int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha, const pog_options *opt,
+                     void *stream, pog_graph **out, Launch launch) {
+    const VolumeSpec v{X, Y, Z, delta, alpha};
+    return build_batch(1, &v, opt, stream, out, [&](int, const Grid &g, cudaStream_t st) { return launch(g, st); });
 }
 
 }  // namespace
@@ -296,14 +389,14 @@ extern "C" {
 pog_status pog_build(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha,
                      const pog_options *opt, void *stream, pog_graph **out) {
     if (!cost_dev) return POG_E_INVALID;
-    return build_impl(X, Y, Z, delta, alpha, opt, stream, out,
-                      [&](const Grid &g, cudaStream_t st) { return pog::launch_build_i32(g, cost_dev, st); });
+    return build_one(X, Y, Z, delta, alpha, opt, stream, out,
+                     [&](const Grid &g, cudaStream_t st) { return pog::launch_build_i32(g, cost_dev, st); });
 }
 
 pog_status pog_build_f32(const float *cost_dev, float scale, int32_t X, int32_t Y, int32_t Z, int32_t delta,
                          int32_t alpha, const pog_options *opt, void *stream, pog_graph **out) {
     if (!cost_dev || !(scale > 0.0f)) return POG_E_INVALID;
-    return build_impl(X, Y, Z, delta, alpha, opt, stream, out, [&](const Grid &g, cudaStream_t st) {
+    return build_one(X, Y, Z, delta, alpha, opt, stream, out, [&](const Grid &g, cudaStream_t st) {
         return pog::launch_build_f32(g, cost_dev, scale, nullptr, 0, st);
     });
 }
@@ -312,7 +405,7 @@ pog_status pog_build_f32_augmented(const float *cost_dev, float scale, const int
                                    int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha,
                                    const pog_options *opt, void *stream, pog_graph **out) {
     if (!cost_dev || !h_aug_dev || !(scale > 0.0f) || margin < 0 || margin >= (1 << 28)) return POG_E_INVALID;
-    return build_impl(X, Y, Z, delta, alpha, opt, stream, out, [&](const Grid &g, cudaStream_t st) {
+    return build_one(X, Y, Z, delta, alpha, opt, stream, out, [&](const Grid &g, cudaStream_t st) {
         return pog::launch_build_f32(g, cost_dev, scale, h_aug_dev, margin, st);
     });
 }
@@ -322,7 +415,7 @@ pog_status pog_energy(const pog_graph *g, int64_t *energy_out) {
     if (!g->solved) return POG_E_STATE;
     // max-flow = E*(h) + K with K = -1 - sum_col c(col,0) + sum_{w<0} (-w) (the cut of
     // the closed set below h, Eq. 6, after the weights telescope along each column).
-    const DevCounters &c = *g->ctr_host;
+    const DevCounters &c = volume_counters(g, 0);
     const long long K = -1 - (long long)c.bottom_sum + (long long)c.src_total + (long long)c.neg_bottom;
     *energy_out = g->flow - K;
     return POG_OK;
@@ -341,7 +434,9 @@ pog_status pog_surface_energy(const float *cost_dev, float scale, const int32_t 
 pog_status pog_maxflow(pog_graph *g, int64_t *flow_out) {
     if (!g || !flow_out) return POG_E_INVALID;
     g->solved = 0;
-    return maxflow_impl(g, flow_out);
+    const pog_status s = maxflow_impl(g);
+    if (s == POG_OK) *flow_out = g->flow;
+    return s;
 }
 
 pog_status pog_surface(pog_graph *g, int32_t *heights_dev) {
@@ -360,9 +455,9 @@ pog_status pog_stats(const pog_graph *g, pog_stats_t *out) {
     out->cut_passes = g->stats[ST_CUT];
     out->gaps = g->stats[ST_GAPS];
     out->active_initial = g->stats[ST_ACTIVE0];
-    out->launches = g->stats[ST_LAUNCHES] + 1;
+    out->launches = g->stats[ST_LAUNCHES];
     out->tiles_visited = (long long)g->ctr_host->tiles_visited;
-    out->nodes = g->N;
+    out->nodes = g->n_total;
     out->state_bytes = (long long)g->arena_bytes;
     if (g->timers[TM_BUILD].used) {  // the build was timed; its events are complete after pog_maxflow
         if (cudaStreamSynchronize(g->stream) != cudaSuccess) return POG_E_CUDA;
@@ -430,8 +525,13 @@ void pog_free(pog_graph *g) {
     }
     for (auto ev : g->round_ev)
         if (ev) cudaEventDestroy(ev);
-    cudaFree(g->arena);
-    cudaFreeHost(g->ctr_host);
+    if (g->arena) cudaFree(g->arena);
+    if (g->ctr_host) cudaFreeHost(g->ctr_host);
+    delete[] g->vols;
+    delete[] g->node_base;
+    delete[] g->tile_base;
+    delete[] g->col_base;
+    delete[] g->flows;
     delete g;
 }
 
@@ -478,17 +578,34 @@ pog_status pog_backward(float *grad_dev, const int32_t *h_dev, const int32_t *h_
 pog_status pog_solve_batch(int32_t n, const pog_volume *vols, const pog_options *opt, void *stream,
                            int64_t *flows_out, int32_t *const *heights_dev) {
     if (n < 0 || (n > 0 && (!vols || !flows_out || !heights_dev))) return POG_E_INVALID;
-    pog_status first = POG_OK;
+    if (n == 0) return POG_OK;
+    if (n > pog::kMaxVolumes) return POG_E_INVALID;
+    VolumeSpec *spec = new (std::nothrow) VolumeSpec[n];
+    if (!spec) return POG_E_NOMEM;
     for (int i = 0; i < n; ++i) {
-        pog_graph *g = nullptr;
-        const pog_volume &v = vols[i];
-        pog_status s = pog_build(v.cost_dev, v.X, v.Y, v.Z, v.delta, v.alpha, opt, stream, &g);
-        if (s == POG_OK) s = pog_maxflow(g, &flows_out[i]);
-        if (s == POG_OK) s = pog_surface(g, heights_dev[i]);
-        pog_free(g);
-        if (s != POG_OK && first == POG_OK) first = s;
+        if (!vols[i].cost_dev || !heights_dev[i]) {
+            delete[] spec;
+            return POG_E_INVALID;
+        }
+        spec[i] = VolumeSpec{vols[i].X, vols[i].Y, vols[i].Z, vols[i].delta, vols[i].alpha};
     }
-    return first;
+    pog_graph *g = nullptr;
+    pog_status s = build_batch(n, spec, opt, stream, &g, [&](int v, const Grid &gr, cudaStream_t st) {
+        return pog::launch_build_i32(gr, vols[v].cost_dev, st);
+    });
+    delete[] spec;
+    if (s != POG_OK) return s;
+    s = maxflow_impl(g);
+    if (s == POG_OK) {
+        for (int i = 0; i < n && s == POG_OK; ++i) {
+            flows_out[i] = g->flows[i];
+            s = from_cuda(cudaMemcpyAsync(heights_dev[i], g->heights + g->col_base[i],
+                                          sizeof(int32_t) * (size_t)vols[i].X * vols[i].Y, cudaMemcpyDeviceToDevice,
+                                          g->stream));
+        }
+    }
+    pog_free(g);  // synchronises the stream first
+    return s;
 }
 
 }  // extern "C"

@@ -92,27 +92,48 @@ __device__ __forceinline__ void decode(const Grid &g, int u, int &x, int &y, int
     y = col - x * g.Y;
 }
 
-template <bool SOFT>
-__global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa, int *qb, BfsSync *sync,
+template <bool RO>
+__device__ __forceinline__ void gather_in_any(const Grid &g, int v, int x, int y, int z, Hood &h) {
+    if (g.gs[0]) gather_in<true, RO>(g, v, x, y, z, h);
+    else gather_in<false, RO>(g, v, x, y, z, h);
+}
+
+template <bool RO>
+__device__ __forceinline__ void gather_out_any(const Grid &g, int u, int x, int y, int z, Hood &h) {
+    if (g.gs[0]) gather_out<true, RO>(g, u, x, y, z, h);
+    else gather_out<false, RO>(g, u, x, y, z, h);
+}
+
+// Union node bases of the batch in shared memory (kMaxVolumes + 1 ints).
+__device__ __forceinline__ void load_bases(const Batch &b, int *sbase) {
+    for (int i = threadIdx.x; i <= b.nvol; i += blockDim.x) sbase[i] = b.node_base[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, int *qa, int *qb, BfsSync *sync,
                                                                 int bottom_up_ratio) {
+    __shared__ int sbase[kMaxVolumes + 1];
     const unsigned nblocks = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    int *err = &g.ctr->error;
+    int *err = &b.ctr->error;
     BfsSync *s = sync;
+    load_bases(b, sbase);
+    long long unvisited = 0;
     // level 1: nodes whose sink arc is residual; everything else starts unreachable
-    for (int base = blockIdx.x * blockDim.x; base < g.N; base += stride) {
-        const int u = base + threadIdx.x;
-        if (u < g.N) {
+    for (int v = 0; v < b.nvol; ++v) {
+        const Grid g = b.vols[v];
+        const int base = sbase[v];
+        unvisited += (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
+        for (int u = tid; u < g.N; u += stride) {
             const bool first = (u % g.Z != 0) && g.snk[u] > 0;
             g.lab[u] = first ? 1 : POG_INF;
-            if (first) warp_append(u, qa, &s->size[1]);
+            if (first) warp_append(base + u, qa, &s->size[1]);
         }
     }
     if (!grid_sync(s, nblocks, err)) return;
     int level = 1;
     int *cur = qa, *nxt = qb;
-    long long unvisited = (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
     __shared__ int frontier;
     for (;;) {
         if (threadIdx.x == 0) frontier = *(volatile int *)&s->size[level % 3];
@@ -124,42 +145,51 @@ __global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa,
         const bool bottom_up = bottom_up_ratio > 0 && (long long)n * bottom_up_ratio > unvisited;
         if (tid == 0) {
             s->size[(level + 2) % 3] = 0;  // level-1's counter, free again
-            if (g.trace && level <= kTraceLevels) {
+            if (b.trace && level <= kTraceLevels) {
                 unsigned long long t;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                g.trace[level - 1] = LevelTrace{n, bottom_up ? 1 : 0, (long long)t, 0};
+                b.trace[level - 1] = LevelTrace{n, bottom_up ? 1 : 0, (long long)t, 0};
             }
         }
         if (bottom_up) {
             // bottom-up: every unlabelled node looks for a residual arc into this level;
             // neighbours sit at a fixed offset across a warp, so every load is coalesced
-            for (int u = tid; u < g.N; u += stride) {
-                if (ldcg(g.lab + u) != POG_INF) continue;
-                int x, y, z;
-                decode(g, u, x, y, z);
-                if (z == 0) continue;
-                Hood hd;
-                gather_out<SOFT, true>(g, u, x, y, z, hd);
-                bool hit = false;
+            for (int vi = 0; vi < b.nvol; ++vi) {
+                const Grid g = b.vols[vi];
+                const int base = sbase[vi];
+                for (int u = tid; u < g.N; u += stride) {
+                    if (ldcg(g.lab + u) != POG_INF) continue;
+                    int x, y, z;
+                    decode(g, u, x, y, z);
+                    if (z == 0) continue;
+                    Hood hd;
+                    gather_out_any<true>(g, u, x, y, z, hd);
+                    bool hit = false;
 #pragma unroll
-                for (int k = 0; k < kMaxArcs; ++k) hit |= hd.lab[k] == level;
-                if (hit) {
-                    g.lab[u] = level + 1;
-                    warp_append(u, nxt, &s->size[(level + 1) % 3]);
+                    for (int k = 0; k < kMaxArcs; ++k) hit |= hd.lab[k] == level;
+                    if (hit) {
+                        g.lab[u] = level + 1;
+                        warp_append(base + u, nxt, &s->size[(level + 1) % 3]);
+                    }
                 }
             }
         } else {
             // top-down: expand the frontier queue along residual arcs into its nodes; all
             // claims of a thread are issued together, appends cost one atomic per warp
-            for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-                const int i = base + threadIdx.x;
+            for (int first = blockIdx.x * blockDim.x; first < n; first += stride) {
+                const int i = first + threadIdx.x;
                 unsigned won = 0;
                 Hood hd;
+                int base = 0;
                 if (i < n) {
-                    const int v = cur[i];
+                    const int uv = cur[i];
+                    const int vi = find_volume(sbase, b.nvol, uv);
+                    const Grid g = b.vols[vi];
+                    base = sbase[vi];
+                    const int v = uv - base;
                     int x, y, z;
                     decode(g, v, x, y, z);
-                    gather_in<SOFT, true>(g, v, x, y, z, hd);
+                    gather_in_any<true>(g, v, x, y, z, hd);
                     int old[kMaxArcs];
 #pragma unroll
                     for (int k = 0; k < kMaxArcs; ++k)
@@ -167,8 +197,10 @@ __global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa,
                                      ? atomicCAS(g.lab + hd.node[k], POG_INF, level + 1)
                                      : 0;
 #pragma unroll
-                    for (int k = 0; k < kMaxArcs; ++k)
+                    for (int k = 0; k < kMaxArcs; ++k) {
                         if (hd.res[k] > 0 && hd.lab[k] == POG_INF && old[k] == POG_INF) won |= 1u << k;
+                        hd.node[k] += base;  // to union indices
+                    }
                 }
                 warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
             }
@@ -179,34 +211,39 @@ __global__ void __launch_bounds__(kBfsThreads) k_global_relabel(Grid g, int *qa,
         nxt = t;
         ++level;
     }
-    if (tid == 0 && g.trace && level <= kTraceLevels) {
+    if (tid == 0 && b.trace && level <= kTraceLevels) {
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        g.trace[level - 1] = LevelTrace{0, -1, (long long)t, 0};
+        b.trace[level - 1] = LevelTrace{0, -1, (long long)t, 0};
     }
     // termination test: active nodes (excess > 0 and a finite label)
     unsigned long long active = 0;
-    for (int u = tid; u < g.N; u += stride)
-        if (u % g.Z != 0 && g.exc[u] > 0 && g.lab[u] < POG_INF) ++active;
+    for (int vi = 0; vi < b.nvol; ++vi) {
+        const Grid g = b.vols[vi];
+        for (int u = tid; u < g.N; u += stride)
+            if (u % g.Z != 0 && g.exc[u] > 0 && g.lab[u] < POG_INF) ++active;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(0xffffffffu, active, o);
-    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&g.ctr->active, active);
-    if (tid == 0) g.ctr->max_label = level;
+    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&b.ctr->active, active);
+    if (tid == 0) b.ctr->max_label = level;
 }
 
-template <bool SOFT>
-__global__ void __launch_bounds__(kBfsThreads) k_cut_reach(Grid g, int *qa, int *qb, BfsSync *sync) {
+__global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, int *qa, int *qb, BfsSync *sync) {
+    __shared__ int sbase[kMaxVolumes + 1];
     const unsigned nblocks = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    int *err = &g.ctr->error;
+    int *err = &b.ctr->error;
     BfsSync *s = sync;
-    for (int base = blockIdx.x * blockDim.x; base < g.N; base += stride) {
-        const int u = base + threadIdx.x;
-        if (u < g.N) {
+    load_bases(b, sbase);
+    for (int vi = 0; vi < b.nvol; ++vi) {
+        const Grid g = b.vols[vi];
+        const int base = sbase[vi];
+        for (int u = tid; u < g.N; u += stride) {
             const bool seed = (u % g.Z != 0) && g.exc[u] > 0;
             g.lab[u] = seed ? 1 : 0;
-            if (seed) warp_append(u, qa, &s->size[1]);
+            if (seed) warp_append(base + u, qa, &s->size[1]);
         }
     }
     if (!grid_sync(s, nblocks, err)) return;
@@ -220,22 +257,28 @@ __global__ void __launch_bounds__(kBfsThreads) k_cut_reach(Grid g, int *qa, int 
         __syncthreads();
         if (n == 0) break;
         if (tid == 0) s->size[(level + 2) % 3] = 0;
-        for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-            const int i = base + threadIdx.x;
+        for (int first = blockIdx.x * blockDim.x; first < n; first += stride) {
+            const int i = first + threadIdx.x;
             unsigned won = 0;
             Hood hd;
             if (i < n) {
-                const int u = cur[i];
+                const int uv = cur[i];
+                const int vi = find_volume(sbase, b.nvol, uv);
+                const Grid g = b.vols[vi];
+                const int base = sbase[vi];
+                const int u = uv - base;
                 int x, y, z;
                 decode(g, u, x, y, z);
-                gather_out<SOFT, true>(g, u, x, y, z, hd);
+                gather_out_any<true>(g, u, x, y, z, hd);
                 int old[kMaxArcs];
 #pragma unroll
                 for (int k = 0; k < kMaxArcs; ++k)
                     old[k] = (hd.res[k] > 0 && hd.lab[k] == 0) ? atomicCAS(g.lab + hd.node[k], 0, 1) : 1;
 #pragma unroll
-                for (int k = 0; k < kMaxArcs; ++k)
+                for (int k = 0; k < kMaxArcs; ++k) {
                     if (hd.res[k] > 0 && hd.lab[k] == 0 && old[k] == 0) won |= 1u << k;
+                    hd.node[k] += base;
+                }
             }
             warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
         }
@@ -245,7 +288,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_cut_reach(Grid g, int *qa, int 
         nxt = t;
         ++level;
     }
-    if (tid == 0) g.ctr->max_label = level;
+    if (tid == 0) b.ctr->max_label = level;
 }
 
 // Grid of a cooperative launch: `blocks_per_sm` (default 4) co-resident blocks per SM.
@@ -274,19 +317,17 @@ cudaError_t coop_launch(K kernel, void **args, BfsSync *sync, int blocks_per_sm,
 
 }  // namespace
 
-cudaError_t launch_global_relabel(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+cudaError_t launch_global_relabel(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
                                   int bottom_up_ratio, cudaStream_t st) {
-    Grid gg = g;
-    void *args[] = {&gg, &qa, &qb, &sync, &bottom_up_ratio};
-    if (g.gs[0]) return coop_launch(k_global_relabel<true>, args, sync, blocks_per_sm, st);
-    return coop_launch(k_global_relabel<false>, args, sync, blocks_per_sm, st);
+    Batch bb = b;
+    void *args[] = {&bb, &qa, &qb, &sync, &bottom_up_ratio};
+    return coop_launch(k_global_relabel, args, sync, blocks_per_sm, st);
 }
 
-cudaError_t launch_cut_reach(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
-    Grid gg = g;
-    void *args[] = {&gg, &qa, &qb, &sync};
-    if (g.gs[0]) return coop_launch(k_cut_reach<true>, args, sync, blocks_per_sm, st);
-    return coop_launch(k_cut_reach<false>, args, sync, blocks_per_sm, st);
+cudaError_t launch_cut_reach(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
+    Batch bb = b;
+    void *args[] = {&bb, &qa, &qb, &sync};
+    return coop_launch(k_cut_reach, args, sync, blocks_per_sm, st);
 }
 
 }  // namespace pog

@@ -76,6 +76,34 @@ struct Grid {
     LevelTrace *trace;     // per-level trace of the global relabel (may be null)
 };
 
+// A batch of independent volumes solved as one graph: the disjoint union of their
+// graphs (they share only s and t), so one launch of each kernel serves all of them.
+// Volume v owns union nodes [node_base[v], node_base[v+1]) and union tiles
+// [tile_base[v], tile_base[v+1]); vols[v] views its slice of every union array. A single
+// volume is a batch of one.
+constexpr int kMaxVolumes = 1024;
+
+struct Batch {
+    const Grid *vols;      // device [nvol]
+    const int *node_base;  // device [nvol + 1]
+    const int *tile_base;  // device [nvol + 1] (tiles of the current tile shape)
+    int nvol;
+    int n_total;
+    DevCounters *ctr;      // union counters: active nodes, BFS levels, gap, tile visits, timeouts
+    LevelTrace *trace;     // per-level trace of the last global relabel (may be null)
+};
+
+// Largest v with base[v] <= idx (base ascending, base[0] = 0, nvol entries searched).
+__device__ __forceinline__ int find_volume(const int *base, int nvol, int idx) {
+    int lo = 0, hi = nvol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 enum ArcKind : int { ARC_NONE = -1, ARC_SINK = 0, ARC_DOWN, ARC_UP, ARC_HOUT, ARC_HIN, ARC_SOFT };
 
 __device__ __forceinline__ int ldcg(const int32_t *p) { return __ldcg(p); }
@@ -197,35 +225,40 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
 
 }  // namespace pog
 
-// Host-side graph object behind the opaque pog_graph handle.
+// Host-side graph object behind the opaque pog_graph handle: a batch of nvol volumes
+// (one for pog_build) sharing one device arena.
 struct pog_graph {
-    int X, Y, Z, delta, alpha;
-    long long N;
+    int X, Y, Z, delta, alpha;   // volume 0 (the single-volume API)
+    long long N;                 // nodes of volume 0
+    int nvol;
+    long long n_total;           // nodes of all volumes
+    bool any_soft;
     cudaStream_t stream;
     void *arena;
     size_t arena_bytes;
-    pog::Grid grid;
-    int32_t *heights;            // device [X*Y]
-    int32_t *queue_a, *queue_b;  // device [N] each: BFS frontiers
+    pog::Grid grid;              // view of volume 0
+    pog::Grid *vols;             // host [nvol]: per-volume views
+    pog::Grid *vols_dev;         // device [nvol]
+    int *node_base, *tile_base;  // host [nvol + 1]
+    int *node_base_dev, *tile_base_dev;
+    long long *col_base;         // host [nvol + 1]: first column of each volume in `heights`
+    pog::Batch batch;            // device-side batch view
+    int32_t *heights;            // device [sum of X*Y]
+    int32_t *queue_a, *queue_b;  // device [n_total] each: BFS frontiers
     pog::BfsSync *bfs_sync;      // device: grid barrier + frontier sizes
     pog::LevelTrace *trace;      // device [kTraceLevels]: last global relabel
     int32_t *tile_flag;          // device [tiles]: listed in the current tiled sweep
     int32_t *tile_list;          // device [tiles]
     int32_t *tile_work;          // device [2]: listed tiles, next tile to take
-    pog::DevCounters *ctr;       // device
-    pog::DevCounters *ctr_host;  // pinned host mirror
+    pog::DevCounters *ctr;       // device: union counters
+    pog::DevCounters *vctr;      // device [nvol]: per-volume counters
+    pog::DevCounters *ctr_host;  // pinned host mirror of ctr followed by vctr
     int solved;
-    long long flow;
+    long long flow;              // volume 0
+    long long *flows;            // host [nvol]
     int sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks;
     float relabel_factor;
     int tile_shape, bu_ratio;
-    pog::Grid grid_dims() const {
-        pog::Grid d{};
-        d.X = X;
-        d.Y = Y;
-        d.Z = Z;
-        return d;
-    }
     cudaEvent_t round_ev[4];     // global relabel start/stop, sweep block start/stop
     long long stats[8];
     // POG_FLAG_TIMING: event pairs per kernel family, folded into ms[] after a sync

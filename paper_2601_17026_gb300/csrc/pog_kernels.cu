@@ -251,24 +251,34 @@ __device__ __forceinline__ void discharge(const Grid &g, int u, int ops) {
 // into a list by a coalesced scan, then one thread per listed node discharges it with
 // up to `ops` push or relabel operations. Clustered active nodes thus spread over all
 // threads instead of serialising on the few that own their region.
-__global__ void __launch_bounds__(kThreads) k_collect_active(Grid g, int *list, int *count) {
+__global__ void __launch_bounds__(kThreads) k_collect_active(Batch b, int *list, int *count) {
     const int stride = gridDim.x * blockDim.x;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
-        if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
-        namespace cg = cooperative_groups;
-        const cg::coalesced_group grp = cg::coalesced_threads();
-        int base = 0;
-        if (grp.thread_rank() == 0) base = atomicAdd(count, (int)grp.size());
-        base = grp.shfl(base, 0);
-        list[base + grp.thread_rank()] = u;
+    for (int vi = 0; vi < b.nvol; ++vi) {
+        const Grid g = b.vols[vi];
+        const int base = b.node_base[vi];
+        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
+            if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
+            namespace cg = cooperative_groups;
+            const cg::coalesced_group grp = cg::coalesced_threads();
+            int at = 0;
+            if (grp.thread_rank() == 0) at = atomicAdd(count, (int)grp.size());
+            at = grp.shfl(at, 0);
+            list[at + grp.thread_rank()] = base + u;
+        }
     }
 }
 
-template <bool SOFT>
-__global__ void __launch_bounds__(kThreads) k_push_relabel(Grid g, const int *list, const int *count, int ops) {
+__global__ void __launch_bounds__(kThreads) k_push_relabel(Batch b, const int *list, const int *count, int ops) {
     const int n = *count;
     const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) discharge<SOFT>(g, list[i], ops);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int uv = list[i];
+        const int vi = find_volume(b.node_base, b.nvol, uv);
+        const Grid g = b.vols[vi];
+        const int u = uv - b.node_base[vi];
+        if (g.gs[0]) discharge<true>(g, u, ops);
+        else discharge<false>(g, u, ops);
+    }
 }
 
 // ----------------------------------------------------------------------------------
@@ -278,32 +288,36 @@ __global__ void __launch_bounds__(kThreads) k_push_relabel(Grid g, const int *li
 
 constexpr int kGapSharedWords = 256;  // levels below 8192 are gathered per block first
 
-__global__ void k_gap_occupancy(Grid g, unsigned int *bits, int levels) {
+__global__ void k_gap_occupancy(Batch b, unsigned int *bits, int levels) {
     __shared__ unsigned int local[kGapSharedWords];
     for (int i = threadIdx.x; i < kGapSharedWords; i += blockDim.x) local[i] = 0u;
     __syncthreads();
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
     int lmax = 0;
-    if (u < g.N && u % g.Z != 0) {
-        const int l = g.lab[u];
-        if (l < kGapSharedWords * 32) atomicOr(local + (l >> 5), 1u << (l & 31));
-        else if (l < levels) atomicOr(bits + (l >> 5), 1u << (l & 31));
-        if (l < POG_INF) lmax = l;
+    for (int vi = 0; vi < b.nvol; ++vi) {
+        const Grid g = b.vols[vi];
+        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
+            if (u % g.Z == 0) continue;
+            const int l = g.lab[u];
+            if (l < kGapSharedWords * 32) atomicOr(local + (l >> 5), 1u << (l & 31));
+            else if (l < levels) atomicOr(bits + (l >> 5), 1u << (l & 31));
+            if (l < POG_INF && l > lmax) lmax = l;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
-    if ((threadIdx.x & 31) == 0 && lmax > 0) atomicMax(&g.ctr->max_label, lmax);
+    if ((threadIdx.x & 31) == 0 && lmax > 0) atomicMax(&b.ctr->max_label, lmax);
     __syncthreads();
     for (int i = threadIdx.x; i < kGapSharedWords; i += blockDim.x)
         if (local[i]) atomicOr(bits + i, local[i]);
 }
 
 // One block: the first empty level above 0 that lies below the largest finite label.
-__global__ void k_gap_find(Grid g, const unsigned int *bits, int levels) {
+__global__ void k_gap_find(Batch b, const unsigned int *bits, int levels) {
     __shared__ int first;
     if (threadIdx.x == 0) first = 0x7fffffff;
     __syncthreads();
-    const int lmax = min(g.ctr->max_label, levels - 1);
+    const int lmax = min(b.ctr->max_label, levels - 1);
     for (int w = threadIdx.x; w * 32 <= lmax; w += blockDim.x) {
         unsigned int empty = ~bits[w];
         if (w == 0) empty &= ~1u;  // level 0 is the sink itself
@@ -313,21 +327,27 @@ __global__ void k_gap_find(Grid g, const unsigned int *bits, int levels) {
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) g.ctr->gap_level = first == 0x7fffffff ? 0 : first;
+    if (threadIdx.x == 0) b.ctr->gap_level = first == 0x7fffffff ? 0 : first;
 }
 
-__global__ void k_gap_raise(Grid g) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gap = g.ctr->gap_level;
+__global__ void k_gap_raise(Batch b) {
+    const int gap = b.ctr->gap_level;
+    const int stride = gridDim.x * blockDim.x;
     unsigned long long r = 0;
-    if (gap > 0 && u < g.N && u % g.Z != 0) {
-        const int l = g.lab[u];
-        if (l > gap && l < POG_INF) {
-            g.lab[u] = POG_INF;
-            r = 1;
+    if (gap > 0) {
+        for (int vi = 0; vi < b.nvol; ++vi) {
+            const Grid g = b.vols[vi];
+            for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
+                if (u % g.Z == 0) continue;
+                const int l = g.lab[u];
+                if (l > gap && l < POG_INF) {
+                    g.lab[u] = POG_INF;
+                    ++r;
+                }
+            }
         }
     }
-    block_add_u64(r, &g.ctr->raised);
+    block_add_u64(r, &b.ctr->raised);
 }
 
 // One warp per column: the top marked node (0 when only the bottom layer is in S).
@@ -458,33 +478,31 @@ cudaError_t launch_column_prepush(const Grid &g, cudaStream_t st) {
     POG_LAUNCH(k_column_prepush, threads, st, g);
 }
 
-int sweep_blocks(const Grid &g) {
+int grid_blocks() {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             sms = 148;
     }
-    const long long need = blocks_for(g.N);
-    const long long cap = (long long)sms * 8;
-    return (int)(need < cap ? need : cap);
+    return sms * 8;
 }
 
-cudaError_t launch_sweep(const Grid &g, int *list, int *count, int ops, cudaStream_t st) {
+cudaError_t launch_sweep(const Batch &b, int *list, int *count, int ops, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    const int blocks = sweep_blocks(g);
-    k_collect_active<<<blocks, kThreads, 0, st>>>(g, list, count);
-    if (g.gs[0]) k_push_relabel<true><<<blocks, kThreads, 0, st>>>(g, list, count, ops);
-    else k_push_relabel<false><<<blocks, kThreads, 0, st>>>(g, list, count, ops);
+    const int blocks = grid_blocks();
+    k_collect_active<<<blocks, kThreads, 0, st>>>(b, list, count);
+    k_push_relabel<<<blocks, kThreads, 0, st>>>(b, list, count, ops);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gap(const Grid &g, unsigned int *bits, int levels, cudaStream_t st) {
+cudaError_t launch_gap(const Batch &b, unsigned int *bits, int levels, cudaStream_t st) {
     cudaMemsetAsync(bits, 0, (size_t)(levels / 32) * sizeof(unsigned int), st);
-    k_gap_occupancy<<<blocks_for(g.N), kThreads, 0, st>>>(g, bits, levels);
-    k_gap_find<<<1, 1024, 0, st>>>(g, bits, levels);
-    k_gap_raise<<<blocks_for(g.N), kThreads, 0, st>>>(g);
+    const int blocks = grid_blocks();
+    k_gap_occupancy<<<blocks, kThreads, 0, st>>>(b, bits, levels);
+    k_gap_find<<<1, 1024, 0, st>>>(b, bits, levels);
+    k_gap_raise<<<blocks, kThreads, 0, st>>>(b);
     return cudaGetLastError();
 }
 

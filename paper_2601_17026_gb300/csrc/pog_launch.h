@@ -7,27 +7,28 @@
 namespace pog {
 
 struct Grid;
+struct Batch;
 struct BfsSync;
 
 cudaError_t launch_build_i32(const Grid &g, const int32_t *cost, cudaStream_t st);
 cudaError_t launch_build_f32(const Grid &g, const float *cost, float scale, const int32_t *h_aug, int margin,
                              cudaStream_t st);
 cudaError_t launch_column_prepush(const Grid &g, cudaStream_t st);
-cudaError_t launch_sweep(const Grid &g, int *list, int *count, int ops, cudaStream_t st);
-cudaError_t launch_gap(const Grid &g, unsigned int *bits, int levels, cudaStream_t st);
+cudaError_t launch_sweep(const Batch &b, int *list, int *count, int ops, cudaStream_t st);
+cudaError_t launch_gap(const Batch &b, unsigned int *bits, int levels, cudaStream_t st);
 cudaError_t launch_heights(const Grid &g, int32_t *heights, cudaStream_t st);
 cudaError_t launch_excess_sum(const Grid &g, cudaStream_t st);
 cudaError_t launch_quantise(const float *in, int32_t *out, long long n, float scale, int *err, cudaStream_t st);
 cudaError_t launch_backward(float *grad, const int32_t *h, const int32_t *ht, const int32_t *hh, const float *ge,
                             const float *gh, int B, int XY, int Z, cudaStream_t st);
-cudaError_t launch_global_relabel(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+cudaError_t launch_global_relabel(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
                                   int bottom_up_ratio, cudaStream_t st);
-cudaError_t launch_cut_reach(const Grid &g, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_cut_reach(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st);
 constexpr int kTileShapes = 4;
 long long tile_count(const Grid &g, int shape);
 long long tile_count_max(const Grid &g);
-cudaError_t launch_tile_sweep(const Grid &g, int shape, int *flag, int *list, int *work, int local_sweeps,
-                              cudaStream_t st);
+cudaError_t launch_tile_sweep(const Batch &b, bool soft, int shape, int *flag, int *list, int *work,
+                              int local_sweeps, cudaStream_t st);
 cudaError_t launch_surface_energy(const float *cost, float scale, const int32_t *h, int B, int X, int Y, int Z,
                                   int alpha, long long *out, cudaStream_t st);
 

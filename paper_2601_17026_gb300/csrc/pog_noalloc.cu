@@ -78,14 +78,19 @@ size_t scratch_bytes(int X, int Y, int Z, int alpha) {
     dims.Z = Z;
     const size_t tiles = (size_t)pog::tile_count_max(dims);
     return (arrays + 2) * align_up(N * 4, 256) + 2 * align_up(tiles * 4, 256) + 256 +
-           align_up(sizeof(pog::BfsSync), 256) + align_up(sizeof(pog::DevCounters), 256) + kGapLevels / 8;
+           align_up(sizeof(pog::BfsSync), 256) + 2 * align_up(sizeof(pog::DevCounters), 256) + kGapLevels / 8 +
+           align_up(sizeof(pog::Grid), 256) + 2 * 256;
 }
 
-pog_status read_counters(const pog::Grid &g, pog::DevCounters &host, cudaStream_t st) {
-    NA_TRY_CUDA(cudaMemcpyAsync(&host, g.ctr, sizeof(host), cudaMemcpyDeviceToHost, st));
+// The union counters (`host[0]`) and the volume's counters (`host[1]`) to host memory.
+pog_status read_counters(const pog::DevCounters *uctr, const pog::DevCounters *vctr, pog::DevCounters *host,
+                         cudaStream_t st) {
+    NA_TRY_CUDA(cudaMemcpyAsync(host, uctr, sizeof(*host), cudaMemcpyDeviceToHost, st));
+    NA_TRY_CUDA(cudaMemcpyAsync(host + 1, vctr, sizeof(*host), cudaMemcpyDeviceToHost, st));
     NA_TRY_CUDA(cudaStreamSynchronize(st));
-    if (host.error & POG_ERR_TIMEOUT) return POG_E_TIMEOUT;
-    if (host.error) return POG_E_OVERFLOW;
+    const int err = host[0].error | host[1].error;
+    if (err & POG_ERR_TIMEOUT) return POG_E_TIMEOUT;
+    if (err) return POG_E_OVERFLOW;
     return POG_OK;
 }
 
@@ -133,44 +138,60 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     int32_t *tile_list = c.take<int32_t>(tiles * 4);
     int32_t *tile_work = c.take<int32_t>(256);
     pog::BfsSync *sync = c.take<pog::BfsSync>(sizeof(pog::BfsSync));
+    pog::DevCounters *uctr = c.take<pog::DevCounters>(sizeof(pog::DevCounters));
+    unsigned int *gap_bits = c.take<unsigned int>(kGapLevels / 8);  // right after the union counters
     g.ctr = c.take<pog::DevCounters>(sizeof(pog::DevCounters));
-    unsigned int *gap_bits = c.take<unsigned int>(kGapLevels / 8);
     g.trace = nullptr;
+    pog::Grid *vol_table = c.take<pog::Grid>(sizeof(pog::Grid));
+    int *node_base = c.take<int>(2 * sizeof(int));
+    int *tile_base = c.take<int>(2 * sizeof(int));
+    pog::Batch b{};
+    b.vols = vol_table;
+    b.node_base = node_base;
+    b.tile_base = tile_base;
+    b.nvol = 1;
+    b.n_total = (int)N;
+    b.ctr = uctr;
+    b.trace = nullptr;
+    const int bases[2] = {0, (int)N};
+    const int tbases[2] = {0, (int)pog::tile_count(g, shape)};
 
     // The array keeps the previous call's contents: clear what must start at zero.
+    NA_TRY_CUDA(cudaMemcpyAsync(vol_table, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+    NA_TRY_CUDA(cudaMemcpyAsync(node_base, bases, sizeof(bases), cudaMemcpyHostToDevice, st));
+    NA_TRY_CUDA(cudaMemcpyAsync(tile_base, tbases, sizeof(tbases), cudaMemcpyHostToDevice, st));
+    NA_TRY_CUDA(cudaMemsetAsync(uctr, 0, sizeof(pog::DevCounters), st));
     NA_TRY_CUDA(cudaMemsetAsync(g.ctr, 0, sizeof(pog::DevCounters), st));
     NA_TRY_CUDA(cudaMemsetAsync(tile_flag, 0, tiles * 4, st));
     NA_TRY_CUDA(pog::launch_build_i32(g, cost_dev, st));
 
-    pog::DevCounters host;
-    std::memset(&host, 0, sizeof host);
-    NA_TRY(read_counters(g, host, st));
+    pog::DevCounters host[2];
+    std::memset(host, 0, sizeof host);
+    NA_TRY(read_counters(uctr, g.ctr, host, st));
     if (!(flags & POG_FLAG_NO_PREPUSH)) NA_TRY_CUDA(pog::launch_column_prepush(g, st));
-    const size_t active_off = offsetof(pog::DevCounters, active);
+    const bool soft = alpha > 0;
     for (int round = 0;; ++round) {
-        NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + active_off, 0, sizeof(host.active), st));
-        NA_TRY_CUDA(pog::launch_global_relabel(g, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
-        NA_TRY(read_counters(g, host, st));
-        if (host.active == 0) break;
+        NA_TRY_CUDA(cudaMemsetAsync(&uctr->active, 0, sizeof(host[0].active), st));
+        NA_TRY_CUDA(pog::launch_global_relabel(b, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
+        NA_TRY(read_counters(uctr, g.ctr, host, st));
+        if (host[0].active == 0) break;
         if (round + 1 >= max_rounds) return POG_E_NOCONVERGE;
         for (int k = 0; k < sweeps; ++k) {
             if (flags & POG_FLAG_NODE_SWEEPS)
-                NA_TRY_CUDA(pog::launch_sweep(g, queue_a, &sync->size[0], kNodeOps, st));
+                NA_TRY_CUDA(pog::launch_sweep(b, queue_a, &sync->size[0], kNodeOps, st));
             else
-                NA_TRY_CUDA(pog::launch_tile_sweep(g, shape, tile_flag, tile_list, tile_work, tile_sweeps, st));
+                NA_TRY_CUDA(pog::launch_tile_sweep(b, soft, shape, tile_flag, tile_list, tile_work, tile_sweeps, st));
             if (!(flags & POG_FLAG_NO_GAP) && k + 1 == sweeps / 2) {
-                NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + offsetof(pog::DevCounters, max_label),
-                                            0, sizeof(int), st));
-                NA_TRY_CUDA(pog::launch_gap(g, gap_bits, kGapLevels, st));
+                NA_TRY_CUDA(cudaMemsetAsync(&uctr->max_label, 0, sizeof(int), st));
+                NA_TRY_CUDA(pog::launch_gap(b, gap_bits, kGapLevels, st));
             }
         }
     }
-    NA_TRY_CUDA(pog::launch_cut_reach(g, queue_a, queue_b, sync, bfs_blocks, st));
+    NA_TRY_CUDA(pog::launch_cut_reach(b, queue_a, queue_b, sync, bfs_blocks, st));
     NA_TRY_CUDA(pog::launch_heights(g, heights_dev, st));
-    NA_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(g.ctr) + offsetof(pog::DevCounters, excess_sum), 0,
-                                sizeof(host.excess_sum), st));
+    NA_TRY_CUDA(cudaMemsetAsync(&g.ctr->excess_sum, 0, sizeof(host[1].excess_sum), st));
     NA_TRY_CUDA(pog::launch_excess_sum(g, st));
-    NA_TRY(read_counters(g, host, st));
-    *flow_out = (long long)host.bottom_const + (long long)host.src_total - (long long)host.excess_sum;
+    NA_TRY(read_counters(uctr, g.ctr, host, st));
+    *flow_out = (long long)host[1].bottom_const + (long long)host[1].src_total - (long long)host[1].excess_sum;
     return POG_OK;
 }

@@ -40,28 +40,31 @@ TileGeom geom(const Grid &g, int shape) {
                     (g.Z + sh[2] - 1) / sh[2]};
 }
 
-__device__ __forceinline__ int tile_of(const Grid &g, const TileGeom &t, int u) {
-    const int z = u % g.Z;
-    const int col = u / g.Z;
-    const int x = col / g.Y, y = col - x * g.Y;
-    return ((x / t.tx) * t.nty + (y / t.ty)) * t.ntz + z / t.tz;
-}
-
-__global__ void __launch_bounds__(256) k_collect_tiles(Grid g, TileGeom t, int *flag, int *list, int *count) {
+// List every tile (union numbering) that holds an active node, once.
+__global__ void __launch_bounds__(256) k_collect_tiles(Batch b, int tx, int ty, int tz, int *flag, int *list,
+                                                       int *count) {
     const int stride = gridDim.x * blockDim.x;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
-        if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
-        const int tile = tile_of(g, t, u);
-        if (__ldcg(flag + tile)) continue;
-        if (atomicExch(flag + tile, 1) == 0) list[atomicAdd(count, 1)] = tile;
+    for (int vi = 0; vi < b.nvol; ++vi) {
+        const Grid g = b.vols[vi];
+        const int tbase = b.tile_base[vi];
+        const int nty = (g.Y + ty - 1) / ty, ntz = (g.Z + tz - 1) / tz;
+        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
+            if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
+            const int z = u % g.Z;
+            const int col = u / g.Z;
+            const int x = col / g.Y, y = col - x * g.Y;
+            const int tile = tbase + ((x / tx) * nty + (y / ty)) * ntz + z / tz;
+            if (__ldcg(flag + tile)) continue;
+            if (atomicExch(flag + tile, 1) == 0) list[atomicAdd(count, 1)] = tile;
+        }
     }
 }
 
 // Far end of arc slot k of node (x, y, z) (slots as in gather_out: 0 down, 1 up, then per
 // direction d: 2+3d hard out, 3+3d reverse of the neighbour's hard arc, 4+3d soft);
-// false when the arc does not exist.
-template <bool SOFT>
-__device__ __forceinline__ bool far_node(const Grid &g, int k, int x, int y, int z, int &x2, int &y2, int &z2) {
+// false when the arc does not exist (soft arcs exist only when `soft`).
+__device__ __forceinline__ bool far_node(const Grid &g, bool soft, int k, int x, int y, int z, int &x2, int &y2,
+                                         int &z2) {
     x2 = x;
     y2 = y;
     if (k == 0) {
@@ -85,7 +88,7 @@ __device__ __forceinline__ bool far_node(const Grid &g, int k, int x, int y, int
         return z2 < g.Z;
     }
     z2 = z;
-    return SOFT;
+    return soft;
 }
 
 // Shared-memory image of a tile: current values and the values at load time (for the
@@ -107,27 +110,37 @@ struct Where {
     int gidx;  // global node index
 };
 
+// SOFT: the shared image has room for soft arcs (some volume of the batch has alpha > 0);
+// whether a given tile uses them is decided per volume.
 template <int TX, int TY, int TZ, bool SOFT>
-__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, TileGeom tg, const int *list,
-                                                                    const int *count, int *flag, int *next,
-                                                                    int local_sweeps) {
+__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, const int *list, const int *count,
+                                                                    int *flag, int *next, int local_sweeps) {
     extern __shared__ int4 smem_raw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
     TileSoft &SS = *reinterpret_cast<TileSoft *>(reinterpret_cast<char *>(smem_raw) + sizeof(TileSmem));
-    __shared__ int tile_id;
+    __shared__ int tile_id, local_tile;
+    __shared__ Grid sg;
     const int ntiles = *count;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const int slot = atomicAdd(next, 1);
             tile_id = slot < ntiles ? list[slot] : -1;
+            if (tile_id >= 0) {
+                const int vi = find_volume(b.tile_base, b.nvol, tile_id);
+                sg = b.vols[vi];
+                local_tile = tile_id - b.tile_base[vi];
+            }
         }
         __syncthreads();
         const int tile = tile_id;
         if (tile < 0) return;
-        const int tz = tile % tg.ntz;
-        const int txy = tile / tg.ntz;
-        const int x0 = (txy / tg.nty) * TX, y0 = (txy % tg.nty) * TY, z0 = tz * TZ;
+        const Grid &g = sg;
+        const bool soft = SOFT && g.gs[0] != nullptr;
+        const int nty = (g.Y + TY - 1) / TY, ntz = (g.Z + TZ - 1) / TZ;
+        const int tz = local_tile % ntz;
+        const int txy = local_tile / ntz;
+        const int x0 = (txy / nty) * TX, y0 = (txy % nty) * TY, z0 = tz * TZ;
         if (threadIdx.x == 0) flag[tile] = 0;  // the tile may be listed again by a later scan
 
         // ---- load (coalesced along z)
@@ -155,7 +168,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
                 S.fh[d][s] = v;
                 S.fh0[d][s] = v;
             }
-            if (SOFT) {
+            if (soft) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const int v = own[k] ? ldcg(g.gs[j] + u) : 0;
@@ -211,7 +224,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
                     int x2, y2, z2;
                     res[k] = 0;
                     far_lab[k] = POG_INF;
-                    if (!far_node<SOFT>(g, k, x, y, z, x2, y2, z2)) continue;
+                    if (!far_node(g, soft, k, x, y, z, x2, y2, z2)) continue;
                     const Where w = where(x2, y2, z2);
                     const int d = k >= 2 ? (k - 2) / 3 : 0;
                     const int kind = k < 2 ? k : 2 + (k - 2) % 3;  // 0 down, 1 up, 2 hout, 3 hin, 4 soft
@@ -236,7 +249,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
                     continue;
                 }
                 int x2, y2, z2;
-                far_node<SOFT>(g, bk, x, y, z, x2, y2, z2);
+                far_node(g, soft, bk, x, y, z, x2, y2, z2);
                 const Where bw = where(x2, y2, z2);
                 const int bd = bk >= 2 ? (bk - 2) / 3 : 0;
                 const int bkind = bk < 2 ? bk : 2 + (bk - 2) % 3;
@@ -269,7 +282,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
             if (!__any_sync(0xffffffffu, busy)) break;
         }
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&g.ctr->tiles_visited, 1ull);
+        if (threadIdx.x == 0) atomicAdd(&b.ctr->tiles_visited, 1ull);
 
         // ---- write back: owner-only words by store, shared words as deltas
 #pragma unroll
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Grid g, T
                 d = S.fh[j][s] - S.fh0[j][s];
                 if (d) atomicAdd(g.fh[j] + u, d);
             }
-            if (SOFT) {
+            if (soft) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     d = SS.gs[j][s] - SS.gs0[j][s];
@@ -323,9 +336,8 @@ long long tile_count_max(const Grid &g) {
 }
 
 template <int TX, int TY, int TZ>
-cudaError_t launch_tile_kernel(const Grid &g, const TileGeom &t, int *flag, int *list, int *work, int local_sweeps,
+cudaError_t launch_tile_kernel(const Batch &b, bool soft, int *flag, int *list, int *work, int local_sweeps,
                                int blocks, cudaStream_t st) {
-    const bool soft = g.gs[0] != nullptr;
     const size_t smem = sizeof(TileSmem) + (soft ? sizeof(TileSoft) : 0);
     static bool configured[2] = {false, false};
     cudaError_t e = cudaSuccess;
@@ -338,31 +350,32 @@ cudaError_t launch_tile_kernel(const Grid &g, const TileGeom &t, int *flag, int 
         configured[soft] = true;
     }
     if (soft)
-        k_tile_push_relabel<TX, TY, TZ, true><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1,
+        k_tile_push_relabel<TX, TY, TZ, true><<<blocks, kTileThreads, smem, st>>>(b, list, work, flag, work + 1,
                                                                                  local_sweeps);
     else
-        k_tile_push_relabel<TX, TY, TZ, false><<<blocks, kTileThreads, smem, st>>>(g, t, list, work, flag, work + 1,
+        k_tile_push_relabel<TX, TY, TZ, false><<<blocks, kTileThreads, smem, st>>>(b, list, work, flag, work + 1,
                                                                                   local_sweeps);
     return cudaGetLastError();
 }
 
-// One tiled sweep: list the tiles that hold an active node, then let persistent blocks
-// take tiles from the list. `work` holds [count, next]; `flag` is one int per tile and
-// must start zeroed (each visited tile clears its own flag).
-cudaError_t launch_tile_sweep(const Grid &g, int shape, int *flag, int *list, int *work, int local_sweeps,
-                              cudaStream_t st) {
+// One tiled sweep over every volume of the batch: list the tiles that hold an active
+// node, then let persistent blocks take tiles from the list. `work` holds [count, next];
+// `flag` is one int per union tile and must start zeroed (visited tiles clear theirs).
+// `soft`: some volume has alpha > 0.
+cudaError_t launch_tile_sweep(const Batch &b, bool soft, int shape, int *flag, int *list, int *work,
+                              int local_sweeps, cudaStream_t st) {
     if (shape < 0 || shape >= kTileShapes) shape = 0;
-    const TileGeom t = geom(g, shape);
     cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
-    k_collect_tiles<<<sms * 8, 256, 0, st>>>(g, t, flag, list, work);
+    const int *sh = kShapes[shape];
+    k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag, list, work);
     const int blocks = sms * 3;
     switch (shape) {
-        case 1: return launch_tile_kernel<8, 8, 16>(g, t, flag, list, work, local_sweeps, blocks, st);
-        case 2: return launch_tile_kernel<4, 4, 64>(g, t, flag, list, work, local_sweeps, blocks, st);
-        case 3: return launch_tile_kernel<2, 4, 128>(g, t, flag, list, work, local_sweeps, blocks, st);
-        default: return launch_tile_kernel<4, 8, 32>(g, t, flag, list, work, local_sweeps, blocks, st);
+        case 1: return launch_tile_kernel<8, 8, 16>(b, soft, flag, list, work, local_sweeps, blocks, st);
+        case 2: return launch_tile_kernel<4, 4, 64>(b, soft, flag, list, work, local_sweeps, blocks, st);
+        case 3: return launch_tile_kernel<2, 4, 128>(b, soft, flag, list, work, local_sweeps, blocks, st);
+        default: return launch_tile_kernel<4, 8, 32>(b, soft, flag, list, work, local_sweeps, blocks, st);
     }
 }
 
