@@ -119,20 +119,51 @@ void fold_timers(pog_graph *g) {
     }
 }
 
-// Global relabel (exact reverse BFS from t, one cooperative launch for the whole batch)
+// Drop from `live` the volumes whose last relabel found no active node: a volume with none
+// never changes again (no tile of it is listed, nothing pushes into it, it shares no arc
+// with another volume), so later relabels, sweeps and gap passes skip it.
+pog_status shrink_live(pog_graph *g) {
+    int n = 0;
+    bool changed = false;
+    for (int i = 0; i < g->nlive; ++i) {
+        const int v = g->live_ids[i];
+        if (volume_counters(g, v).active == 0) {
+            changed = true;
+            continue;
+        }
+        g->live_ids[n] = v;
+        g->live_vols[n] = g->vols[v];
+        g->live_node_base[n] = g->node_base[v];
+        g->live_tile_base[n] = g->tile_base[v];
+        ++n;
+    }
+    if (!changed || n == 0) return POG_OK;
+    g->nlive = n;
+    POG_TRY_CUDA(cudaMemcpyAsync(g->live_vols_dev, g->live_vols, sizeof(Grid) * n, cudaMemcpyHostToDevice, g->stream));
+    POG_TRY_CUDA(cudaMemcpyAsync(g->live_node_base_dev, g->live_node_base, sizeof(int) * n, cudaMemcpyHostToDevice,
+                                 g->stream));
+    POG_TRY_CUDA(cudaMemcpyAsync(g->live_tile_base_dev, g->live_tile_base, sizeof(int) * n, cudaMemcpyHostToDevice,
+                                 g->stream));
+    POG_TRY_CUDA(cudaStreamSynchronize(g->stream));  // the host tables are rewritten next round
+    g->live.nvol = n;
+    return POG_OK;
+}
+
+// Global relabel (exact reverse BFS from t, one cooperative launch for the live volumes)
 // fused with the termination count; returns the number of active nodes.
 pog_status global_relabel(pog_graph *g, long long &active) {
     POG_TRY(reset_field(g, &DevCounters::active));
     POG_TRY_CUDA(cudaEventRecord(g->round_ev[0], g->stream));
     POG_TRY_CUDA(timed(g, TM_BFS, [&] {
-        return pog::launch_global_relabel(g->batch, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->bu_ratio,
-                                          g->stream);
+        return pog::launch_global_relabel(g->live, g->nlive == 1 ? &g->live_vols[0] : nullptr, g->queue_a,
+                                          g->queue_b, g->bfs_sync, g->bfs_blocks, g->bu_ratio, g->stream);
     }));
     POG_TRY_CUDA(cudaEventRecord(g->round_ev[1], g->stream));
     g->stats[ST_LAUNCHES] += 1;
     POG_TRY(read_counters(g));
     g->stats[ST_BFS] += g->ctr_host->max_label;  // BFS levels of this relabel
     active = (long long)g->ctr_host->active;
+    if (active > 0) POG_TRY(shrink_live(g));
     return POG_OK;
 }
 
@@ -141,8 +172,30 @@ unsigned int *gap_bits(pog_graph *g) {
     return reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(g->ctr) + align_up(sizeof(DevCounters), 256));
 }
 
+pog_status reset_live(pog_graph *g) {
+    g->nlive = g->nvol;
+    for (int v = 0; v < g->nvol; ++v) {
+        g->live_ids[v] = v;
+        g->live_vols[v] = g->vols[v];
+        g->live_node_base[v] = g->node_base[v];
+        g->live_tile_base[v] = g->tile_base[v];
+    }
+    g->live = g->batch;
+    g->live.vols = g->live_vols_dev;
+    g->live.node_base = g->live_node_base_dev;
+    g->live.tile_base = g->live_tile_base_dev;
+    POG_TRY_CUDA(cudaMemcpyAsync(g->live_vols_dev, g->live_vols, sizeof(Grid) * g->nvol, cudaMemcpyHostToDevice,
+                                 g->stream));
+    POG_TRY_CUDA(cudaMemcpyAsync(g->live_node_base_dev, g->live_node_base, sizeof(int) * g->nvol,
+                                 cudaMemcpyHostToDevice, g->stream));
+    POG_TRY_CUDA(cudaMemcpyAsync(g->live_tile_base_dev, g->live_tile_base, sizeof(int) * g->nvol,
+                                 cudaMemcpyHostToDevice, g->stream));
+    return POG_OK;
+}
+
 pog_status maxflow_impl(pog_graph *g) {
     std::memset(g->stats, 0, sizeof g->stats);
+    POG_TRY(reset_live(g));
     g->stats[ST_LAUNCHES] = 2 * g->nvol;  // the builds
     for (int f = TM_SWEEP; f <= TM_CUT; ++f) g->timers[f].ms = 0.0;
     POG_TRY(read_counters(g));  // surfaces build errors (cost range)
@@ -168,14 +221,15 @@ pog_status maxflow_impl(pog_graph *g) {
         for (int k = 0; k < sweeps; ++k) {
             POG_TRY_CUDA(timed(g, TM_SWEEP, [&] {
                 if (g->flags & POG_FLAG_NODE_SWEEPS)
-                    return pog::launch_sweep(g->batch, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
-                return pog::launch_tile_sweep(g->batch, g->any_soft, g->tile_shape, g->tile_flag, g->tile_list,
-                                              g->tile_work, g->tile_sweeps, g->stream);
+                    return pog::launch_sweep(g->live, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
+                return pog::launch_tile_sweep(g->live, g->nlive == 1 ? &g->live_vols[0] : nullptr,
+                                              g->live_tile_base[0], g->any_soft, g->tile_shape, g->tile_flag,
+                                              g->tile_list, g->tile_work, g->tile_sweeps, g->stream);
             }));
             if (gap && k + 1 == half) {
                 POG_TRY(reset_field(g, &DevCounters::raised));
                 POG_TRY(reset_field(g, &DevCounters::max_label));
-                POG_TRY_CUDA(pog::launch_gap(g->batch, gap_bits(g), kGapLevels, g->stream));
+                POG_TRY_CUDA(pog::launch_gap(g->live, gap_bits(g), kGapLevels, g->stream));
                 g->stats[ST_LAUNCHES] += 3;
                 g->stats[ST_GAPS]++;
             }
@@ -196,7 +250,8 @@ pog_status maxflow_impl(pog_graph *g) {
     }
     // Maximum preflow reached: extract the minimal cut, the heights and the flow values.
     POG_TRY_CUDA(timed(g, TM_CUT, [&] {
-        return pog::launch_cut_reach(g->batch, g->queue_a, g->queue_b, g->bfs_sync, g->bfs_blocks, g->stream);
+        return pog::launch_cut_reach(g->batch, g->nvol == 1 ? &g->vols[0] : nullptr, g->queue_a, g->queue_b,
+                                     g->bfs_sync, g->bfs_blocks, g->stream);
     }));
     for (int v = 0; v < g->nvol; ++v) {
         POG_TRY_CUDA(pog::launch_heights(g->vols[v], g->heights + g->col_base[v], g->stream));
@@ -257,7 +312,12 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->tile_base = new (std::nothrow) int[n + 1];
     g->col_base = new (std::nothrow) long long[n + 1];
     g->flows = new (std::nothrow) long long[n]();
-    if (!g->vols || !g->node_base || !g->tile_base || !g->col_base || !g->flows) {
+    g->live_vols = new (std::nothrow) Grid[n]();
+    g->live_node_base = new (std::nothrow) int[n + 1];
+    g->live_tile_base = new (std::nothrow) int[n + 1];
+    g->live_ids = new (std::nothrow) int[n + 1];
+    if (!g->vols || !g->node_base || !g->tile_base || !g->col_base || !g->flows || !g->live_vols ||
+        !g->live_node_base || !g->live_tile_base || !g->live_ids) {
         pog_free(g);
         return POG_E_NOMEM;
     }
@@ -283,7 +343,7 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     const size_t sync = align_up(sizeof(pog::BfsSync), 256);
     const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
     const size_t tile_bytes = align_up(sizeof(int32_t) * (size_t)tiles, 256);
-    const size_t table = align_up(sizeof(Grid) * n, 256) + 2 * align_up(sizeof(int) * (n + 1), 256);
+    const size_t table = 2 * (align_up(sizeof(Grid) * n, 256) + 2 * align_up(sizeof(int) * (n + 1), 256));
     g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 2 * tile_bytes + 256 + table;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
@@ -328,6 +388,9 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->vols_dev = reinterpret_cast<Grid *>(take(align_up(sizeof(Grid) * n, 256)));
     g->node_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
     g->tile_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
+    g->live_vols_dev = reinterpret_cast<Grid *>(take(align_up(sizeof(Grid) * n, 256)));
+    g->live_node_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
+    g->live_tile_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
     g->ctr = reinterpret_cast<DevCounters *>(take(ctr));
     long long soft_off = 0;
     for (int v = 0; v < n; ++v) {
@@ -532,6 +595,10 @@ void pog_free(pog_graph *g) {
     delete[] g->tile_base;
     delete[] g->col_base;
     delete[] g->flows;
+    delete[] g->live_vols;
+    delete[] g->live_node_base;
+    delete[] g->live_tile_base;
+    delete[] g->live_ids;
     delete g;
 }
 

@@ -110,8 +110,9 @@ __device__ __forceinline__ void load_bases(const Batch &b, int *sbase) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, int *qa, int *qb, BfsSync *sync,
-                                                                int bottom_up_ratio) {
+template <bool SINGLE>
+__global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, Grid g0, int *qa, int *qb,
+                                                                   BfsSync *sync, int bottom_up_ratio) {
     __shared__ int sbase[kMaxVolumes + 1];
     const unsigned nblocks = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,10 +120,12 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, int 
     int *err = &b.ctr->error;
     BfsSync *s = sync;
     load_bases(b, sbase);
+    if (blockIdx.x == 0)  // per-volume termination counts, summed at the end
+        for (int v = threadIdx.x; v < b.nvol; v += blockDim.x) b.vols[v].ctr->active = 0;
     long long unvisited = 0;
     // level 1: nodes whose sink arc is residual; everything else starts unreachable
     for (int v = 0; v < b.nvol; ++v) {
-        const Grid g = b.vols[v];
+        const Grid g = SINGLE ? g0 : b.vols[v];
         const int base = sbase[v];
         unvisited += (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
         for (int u = tid; u < g.N; u += stride) {
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, int 
             // bottom-up: every unlabelled node looks for a residual arc into this level;
             // neighbours sit at a fixed offset across a warp, so every load is coalesced
             for (int vi = 0; vi < b.nvol; ++vi) {
-                const Grid g = b.vols[vi];
+                const Grid g = SINGLE ? g0 : b.vols[vi];
                 const int base = sbase[vi];
                 for (int u = tid; u < g.N; u += stride) {
                     if (ldcg(g.lab + u) != POG_INF) continue;
@@ -183,8 +186,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, int 
                 int base = 0;
                 if (i < n) {
                     const int uv = cur[i];
-                    const int vi = find_volume(sbase, b.nvol, uv);
-                    const Grid g = b.vols[vi];
+                    const int vi = SINGLE ? 0 : find_volume(sbase, b.nvol, uv);
+                    const Grid g = SINGLE ? g0 : b.vols[vi];
                     base = sbase[vi];
                     const int v = uv - base;
                     int x, y, z;
@@ -216,20 +219,24 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, int 
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         b.trace[level - 1] = LevelTrace{0, -1, (long long)t, 0};
     }
-    // termination test: active nodes (excess > 0 and a finite label)
-    unsigned long long active = 0;
+    // termination test: active nodes (excess > 0 and a finite label), per volume and in all
     for (int vi = 0; vi < b.nvol; ++vi) {
-        const Grid g = b.vols[vi];
+        const Grid g = SINGLE ? g0 : b.vols[vi];
+        unsigned long long active = 0;
         for (int u = tid; u < g.N; u += stride)
             if (u % g.Z != 0 && g.exc[u] > 0 && g.lab[u] < POG_INF) ++active;
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(0xffffffffu, active, o);
-    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&b.ctr->active, active);
+        for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(0xffffffffu, active, o);
+        if ((threadIdx.x & 31) == 0 && active) {
+            atomicAdd(&g.ctr->active, active);
+            atomicAdd(&b.ctr->active, active);
+        }
+    }
     if (tid == 0) b.ctr->max_label = level;
 }
 
-__global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, int *qa, int *qb, BfsSync *sync) {
+template <bool SINGLE>
+__global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, Grid g0, int *qa, int *qb, BfsSync *sync) {
     __shared__ int sbase[kMaxVolumes + 1];
     const unsigned nblocks = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, int *qa, 
     BfsSync *s = sync;
     load_bases(b, sbase);
     for (int vi = 0; vi < b.nvol; ++vi) {
-        const Grid g = b.vols[vi];
+        const Grid g = SINGLE ? g0 : b.vols[vi];
         const int base = sbase[vi];
         for (int u = tid; u < g.N; u += stride) {
             const bool seed = (u % g.Z != 0) && g.exc[u] > 0;
@@ -263,8 +270,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, int *qa, 
             Hood hd;
             if (i < n) {
                 const int uv = cur[i];
-                const int vi = find_volume(sbase, b.nvol, uv);
-                const Grid g = b.vols[vi];
+                const int vi = SINGLE ? 0 : find_volume(sbase, b.nvol, uv);
+                const Grid g = SINGLE ? g0 : b.vols[vi];
                 const int base = sbase[vi];
                 const int u = uv - base;
                 int x, y, z;
@@ -317,17 +324,22 @@ cudaError_t coop_launch(K kernel, void **args, BfsSync *sync, int blocks_per_sm,
 
 }  // namespace
 
-cudaError_t launch_global_relabel(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
-                                  int bottom_up_ratio, cudaStream_t st) {
+cudaError_t launch_global_relabel(const Batch &b, const Grid *single, int *qa, int *qb, BfsSync *sync,
+                                  int blocks_per_sm, int bottom_up_ratio, cudaStream_t st) {
     Batch bb = b;
-    void *args[] = {&bb, &qa, &qb, &sync, &bottom_up_ratio};
-    return coop_launch(k_global_relabel, args, sync, blocks_per_sm, st);
+    Grid g0 = single ? *single : Grid{};
+    void *args[] = {&bb, &g0, &qa, &qb, &sync, &bottom_up_ratio};
+    if (single) return coop_launch(k_global_relabel<true>, args, sync, blocks_per_sm, st);
+    return coop_launch(k_global_relabel<false>, args, sync, blocks_per_sm, st);
 }
 
-cudaError_t launch_cut_reach(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
+cudaError_t launch_cut_reach(const Batch &b, const Grid *single, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+                             cudaStream_t st) {
     Batch bb = b;
-    void *args[] = {&bb, &qa, &qb, &sync};
-    return coop_launch(k_cut_reach, args, sync, blocks_per_sm, st);
+    Grid g0 = single ? *single : Grid{};
+    void *args[] = {&bb, &g0, &qa, &qb, &sync};
+    if (single) return coop_launch(k_cut_reach<true>, args, sync, blocks_per_sm, st);
+    return coop_launch(k_cut_reach<false>, args, sync, blocks_per_sm, st);
 }
 
 }  // namespace pog

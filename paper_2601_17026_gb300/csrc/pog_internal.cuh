@@ -242,7 +242,13 @@ struct pog_graph {
     int *node_base, *tile_base;  // host [nvol + 1]
     int *node_base_dev, *tile_base_dev;
     long long *col_base;         // host [nvol + 1]: first column of each volume in `heights`
-    pog::Batch batch;            // device-side batch view
+    pog::Batch batch;            // device-side batch view (all volumes)
+    pog::Batch live;             // the volumes that still had active nodes at the last relabel
+    pog::Grid *live_vols_dev;    // device [nvol]: tables of `live`
+    int *live_node_base_dev, *live_tile_base_dev;
+    pog::Grid *live_vols;        // host [nvol]
+    int *live_node_base, *live_tile_base, *live_ids;  // host [nvol + 1]
+    int nlive;
     int32_t *heights;            // device [sum of X*Y]
     int32_t *queue_a, *queue_b;  // device [n_total] each: BFS frontiers
     pog::BfsSync *bfs_sync;      // device: grid barrier + frontier sizes

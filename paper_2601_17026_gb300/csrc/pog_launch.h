@@ -21,14 +21,15 @@ cudaError_t launch_excess_sum(const Grid &g, cudaStream_t st);
 cudaError_t launch_quantise(const float *in, int32_t *out, long long n, float scale, int *err, cudaStream_t st);
 cudaError_t launch_backward(float *grad, const int32_t *h, const int32_t *ht, const int32_t *hh, const float *ge,
                             const float *gh, int B, int XY, int Z, cudaStream_t st);
-cudaError_t launch_global_relabel(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
-                                  int bottom_up_ratio, cudaStream_t st);
-cudaError_t launch_cut_reach(const Batch &b, int *qa, int *qb, BfsSync *sync, int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_global_relabel(const Batch &b, const Grid *single, int *qa, int *qb, BfsSync *sync,
+                                  int blocks_per_sm, int bottom_up_ratio, cudaStream_t st);
+cudaError_t launch_cut_reach(const Batch &b, const Grid *single, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
+                             cudaStream_t st);
 constexpr int kTileShapes = 4;
 long long tile_count(const Grid &g, int shape);
 long long tile_count_max(const Grid &g);
-cudaError_t launch_tile_sweep(const Batch &b, bool soft, int shape, int *flag, int *list, int *work,
-                              int local_sweeps, cudaStream_t st);
+cudaError_t launch_tile_sweep(const Batch &b, const Grid *single, int single_tile_base, bool soft, int shape,
+                              int *flag, int *list, int *work, int local_sweeps, cudaStream_t st);
 cudaError_t launch_surface_energy(const float *cost, float scale, const int32_t *h, int B, int X, int Y, int Z,
                                   int alpha, long long *out, cudaStream_t st);
 

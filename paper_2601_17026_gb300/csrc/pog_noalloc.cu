@@ -172,7 +172,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     const bool soft = alpha > 0;
     for (int round = 0;; ++round) {
         NA_TRY_CUDA(cudaMemsetAsync(&uctr->active, 0, sizeof(host[0].active), st));
-        NA_TRY_CUDA(pog::launch_global_relabel(b, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
+        NA_TRY_CUDA(pog::launch_global_relabel(b, &g, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
         NA_TRY(read_counters(uctr, g.ctr, host, st));
         if (host[0].active == 0) break;
         if (round + 1 >= max_rounds) return POG_E_NOCONVERGE;
@@ -180,14 +180,15 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
             if (flags & POG_FLAG_NODE_SWEEPS)
                 NA_TRY_CUDA(pog::launch_sweep(b, queue_a, &sync->size[0], kNodeOps, st));
             else
-                NA_TRY_CUDA(pog::launch_tile_sweep(b, soft, shape, tile_flag, tile_list, tile_work, tile_sweeps, st));
+                NA_TRY_CUDA(pog::launch_tile_sweep(b, &g, 0, soft, shape, tile_flag, tile_list, tile_work,
+                                                   tile_sweeps, st));
             if (!(flags & POG_FLAG_NO_GAP) && k + 1 == sweeps / 2) {
                 NA_TRY_CUDA(cudaMemsetAsync(&uctr->max_label, 0, sizeof(int), st));
                 NA_TRY_CUDA(pog::launch_gap(b, gap_bits, kGapLevels, st));
             }
         }
     }
-    NA_TRY_CUDA(pog::launch_cut_reach(b, queue_a, queue_b, sync, bfs_blocks, st));
+    NA_TRY_CUDA(pog::launch_cut_reach(b, &g, queue_a, queue_b, sync, bfs_blocks, st));
     NA_TRY_CUDA(pog::launch_heights(g, heights_dev, st));
     NA_TRY_CUDA(cudaMemsetAsync(&g.ctr->excess_sum, 0, sizeof(host[1].excess_sum), st));
     NA_TRY_CUDA(pog::launch_excess_sum(g, st));

@@ -110,11 +110,194 @@ struct Where {
     int gidx;  // global node index
 };
 
-// SOFT: the shared image has room for soft arcs (some volume of the batch has alpha > 0);
-// whether a given tile uses them is decided per volume.
+// One visit of one tile: stage it in shared memory, run the local sweeps, write it back.
+// `g` is the tile's volume, `tile` its union index (for the listing flag), `local_tile`
+// its index within the volume.
 template <int TX, int TY, int TZ, bool SOFT>
-__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, const int *list, const int *count,
-                                                                    int *flag, int *next, int local_sweeps) {
+__device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int tile, int local_tile, int *flag,
+                                           int local_sweeps, TileSmem &S, TileSoft &SS) {
+    const bool soft = SOFT && g.gs[0] != nullptr;
+    const int nty = (g.Y + TY - 1) / TY, ntz = (g.Z + TZ - 1) / TZ;
+    const int tz = local_tile % ntz;
+    const int txy = local_tile / ntz;
+    const int x0 = (txy / nty) * TX, y0 = (txy % nty) * TY, z0 = tz * TZ;
+    if (threadIdx.x == 0) flag[tile] = 0;  // the tile may be listed again by a later scan
+
+    // ---- load (coalesced along z)
+    int node[kPerThread];
+    bool own[kPerThread];
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+        const int s = threadIdx.x + kTileThreads * k;
+        const int c = s / TZ;  // column within the tile
+        const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
+        own[k] = x < g.X && y < g.Y && z < g.Z && z >= 1;
+        node[k] = own[k] ? (x * g.Y + y) * g.Z + z : -1;
+        const int u = node[k];
+        S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
+        const int e = own[k] ? ldcg(g.exc + u) : 0;
+        S.exc[s] = e;
+        S.exc0[s] = e;
+        S.snk[s] = own[k] ? ldcg(g.snk + u) : 0;
+        const int f = own[k] ? ldcg(g.fdn + u) : 0;
+        S.fdn[s] = f;
+        S.fdn0[s] = f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const int v = own[k] ? ldcg(g.fh[d] + u) : 0;
+            S.fh[d][s] = v;
+            S.fh0[d][s] = v;
+        }
+        if (soft) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int v = own[k] ? ldcg(g.gs[j] + u) : 0;
+                SS.gs[j][s] = v;
+                SS.gs0[j][s] = v;
+            }
+        }
+    }
+    __syncthreads();
+
+    // locate node (x, y, z) relative to the tile
+    auto where = [&](int x, int y, int z) {
+        Where w;
+        w.gidx = (x * g.Y + y) * g.Z + z;
+        w.in = x >= x0 && x < x0 + TX && y >= y0 && y < y0 + TY && z >= z0 && z < z0 + TZ;
+        w.s = ((x - x0) * TY + (y - y0)) * TZ + (z - z0);
+        return w;
+    };
+
+    // ---- local sweeps. Warps run them without block barriers (shared atomics keep
+    // the tile consistent, and volatile reads see other warps' progress); a warp stops
+    // early once none of its nodes is active.
+    volatile int *vexc = S.exc;
+    volatile int *vlab = S.lab;
+    for (int it = 0; it < local_sweeps; ++it) {
+        int busy = 0;
+#pragma unroll 1
+        for (int k = 0; k < kPerThread; ++k) {
+            if (!own[k]) continue;
+            const int s = threadIdx.x + kTileThreads * k;
+            const int c = s / TZ;
+            const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
+            const int e = vexc[s];
+            const int h = vlab[s];
+            if (e <= 0 || h >= POG_INF) continue;
+            busy = 1;
+            const int sk = ((volatile int *)S.snk)[s];
+            if (sk > 0) {
+                if (h > 0) {
+                    const int d = e < sk ? e : sk;
+                    S.snk[s] = sk - d;
+                    atomicSub(&S.exc[s], d);
+                } else {
+                    S.lab[s] = 1;
+                }
+                continue;
+            }
+            // gather: residual and far-end label of every arc (slots as in gather_out),
+            // every load issued before any is used
+            int res[kMaxArcs], far_lab[kMaxArcs];
+#pragma unroll
+            for (int k = 0; k < kMaxArcs; ++k) {
+                int x2, y2, z2;
+                res[k] = 0;
+                far_lab[k] = POG_INF;
+                if (!far_node(g, soft, k, x, y, z, x2, y2, z2)) continue;
+                const Where w = where(x2, y2, z2);
+                const int d = k >= 2 ? (k - 2) / 3 : 0;
+                const int kind = k < 2 ? k : 2 + (k - 2) % 3;  // 0 down, 1 up, 2 hout, 3 hin, 4 soft
+                if (kind == 0) res[k] = POG_CAP_INF - ((volatile int *)S.fdn)[s];
+                else if (kind == 1) res[k] = w.in ? ((volatile int *)S.fdn)[w.s] : ldcg(g.fdn + w.gidx);
+                else if (kind == 2) res[k] = POG_CAP_INF - ((volatile int *)S.fh[d])[s];
+                else if (kind == 3) res[k] = w.in ? ((volatile int *)S.fh[d ^ 1])[w.s] : ldcg(g.fh[d ^ 1] + w.gidx);
+                else if (d & 1) res[k] = g.alpha - ((volatile int *)SS.gs[d >> 1])[s];
+                else res[k] = g.alpha + (w.in ? ((volatile int *)SS.gs[d >> 1])[w.s] : ldcg(g.gs[d >> 1] + w.gidx));
+                far_lab[k] = w.in ? vlab[w.s] : ldcg(g.lab + w.gidx);
+            }
+            int best = POG_INF, bk = -1, bres = 0;
+#pragma unroll
+            for (int k = 0; k < kMaxArcs; ++k)
+                if (res[k] > 0 && far_lab[k] < best) {
+                    best = far_lab[k];
+                    bk = k;
+                    bres = res[k];
+                }
+            if (bk < 0 || h <= best) {  // relabel (Algorithm 2)
+                S.lab[s] = best >= POG_INF - 1 ? POG_INF : best + 1;
+                continue;
+            }
+            int x2, y2, z2;
+            far_node(g, soft, bk, x, y, z, x2, y2, z2);
+            const Where bw = where(x2, y2, z2);
+            const int bd = bk >= 2 ? (bk - 2) / 3 : 0;
+            const int bkind = bk < 2 ? bk : 2 + (bk - 2) % 3;
+            const int delta = e < bres ? e : bres;
+            int sat = 0;
+            switch (bkind) {
+                case 0: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
+                case 1:
+                    if (bw.in) atomicSub(&S.fdn[bw.s], delta);
+                    else atomicSub(g.fdn + bw.gidx, delta);
+                    break;
+                case 2: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
+                case 3:
+                    if (bw.in) atomicSub(&S.fh[bd ^ 1][bw.s], delta);
+                    else atomicSub(g.fh[bd ^ 1] + bw.gidx, delta);
+                    break;
+                default:
+                    if (bd & 1) atomicAdd(&SS.gs[bd >> 1][s], delta);
+                    else if (bw.in) atomicSub(&SS.gs[bd >> 1][bw.s], delta);
+                    else atomicSub(g.gs[bd >> 1] + bw.gidx, delta);
+                    break;
+            }
+            atomicSub(&S.exc[s], delta);
+            int old;
+            if (bw.in) old = atomicAdd(&S.exc[bw.s], delta);
+            else old = atomicAdd(g.exc + bw.gidx, delta);
+            if (old > 0x7fffffff - delta) sat = 1;
+            if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
+        }
+        if (!__any_sync(0xffffffffu, busy)) break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&b.ctr->tiles_visited, 1ull);
+
+    // ---- write back: owner-only words by store, shared words as deltas
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+        if (!own[k]) continue;
+        const int s = threadIdx.x + kTileThreads * k;
+        const int u = node[k];
+        g.lab[u] = S.lab[s];
+        g.snk[u] = S.snk[s];
+        int d = S.exc[s] - S.exc0[s];
+        if (d) atomicAdd(g.exc + u, d);
+        d = S.fdn[s] - S.fdn0[s];
+        if (d) atomicAdd(g.fdn + u, d);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            d = S.fh[j][s] - S.fh0[j][s];
+            if (d) atomicAdd(g.fh[j] + u, d);
+        }
+        if (soft) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                d = SS.gs[j][s] - SS.gs0[j][s];
+                if (d) atomicAdd(g.gs[j] + u, d);
+            }
+        }
+    }
+}
+
+// SOFT: the shared image has room for soft arcs (some volume of the batch has alpha > 0);
+// whether a given tile uses them is decided per volume. SINGLE: a batch of one volume,
+// whose view comes in as a kernel parameter (read from the constant bank).
+template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
+__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, Grid g0, int tile_base0,
+                                                                    const int *list, const int *count, int *flag,
+                                                                    int *next, int local_sweeps) {
     extern __shared__ int4 smem_raw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
     TileSoft &SS = *reinterpret_cast<TileSoft *>(reinterpret_cast<char *>(smem_raw) + sizeof(TileSmem));
@@ -126,7 +309,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, 
         if (threadIdx.x == 0) {
             const int slot = atomicAdd(next, 1);
             tile_id = slot < ntiles ? list[slot] : -1;
-            if (tile_id >= 0) {
+            if (!SINGLE && tile_id >= 0) {
                 const int vi = find_volume(b.tile_base, b.nvol, tile_id);
                 sg = b.vols[vi];
                 local_tile = tile_id - b.tile_base[vi];
@@ -135,180 +318,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, 
         __syncthreads();
         const int tile = tile_id;
         if (tile < 0) return;
-        const Grid &g = sg;
-        const bool soft = SOFT && g.gs[0] != nullptr;
-        const int nty = (g.Y + TY - 1) / TY, ntz = (g.Z + TZ - 1) / TZ;
-        const int tz = local_tile % ntz;
-        const int txy = local_tile / ntz;
-        const int x0 = (txy / nty) * TX, y0 = (txy % nty) * TY, z0 = tz * TZ;
-        if (threadIdx.x == 0) flag[tile] = 0;  // the tile may be listed again by a later scan
-
-        // ---- load (coalesced along z)
-        int node[kPerThread];
-        bool own[kPerThread];
-#pragma unroll
-        for (int k = 0; k < kPerThread; ++k) {
-            const int s = threadIdx.x + kTileThreads * k;
-            const int c = s / TZ;  // column within the tile
-            const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
-            own[k] = x < g.X && y < g.Y && z < g.Z && z >= 1;
-            node[k] = own[k] ? (x * g.Y + y) * g.Z + z : -1;
-            const int u = node[k];
-            S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
-            const int e = own[k] ? ldcg(g.exc + u) : 0;
-            S.exc[s] = e;
-            S.exc0[s] = e;
-            S.snk[s] = own[k] ? ldcg(g.snk + u) : 0;
-            const int f = own[k] ? ldcg(g.fdn + u) : 0;
-            S.fdn[s] = f;
-            S.fdn0[s] = f;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                const int v = own[k] ? ldcg(g.fh[d] + u) : 0;
-                S.fh[d][s] = v;
-                S.fh0[d][s] = v;
-            }
-            if (soft) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int v = own[k] ? ldcg(g.gs[j] + u) : 0;
-                    SS.gs[j][s] = v;
-                    SS.gs0[j][s] = v;
-                }
-            }
-        }
-        __syncthreads();
-
-        // locate node (x, y, z) relative to the tile
-        auto where = [&](int x, int y, int z) {
-            Where w;
-            w.gidx = (x * g.Y + y) * g.Z + z;
-            w.in = x >= x0 && x < x0 + TX && y >= y0 && y < y0 + TY && z >= z0 && z < z0 + TZ;
-            w.s = ((x - x0) * TY + (y - y0)) * TZ + (z - z0);
-            return w;
-        };
-
-        // ---- local sweeps. Warps run them without block barriers (shared atomics keep
-        // the tile consistent, and volatile reads see other warps' progress); a warp stops
-        // early once none of its nodes is active.
-        volatile int *vexc = S.exc;
-        volatile int *vlab = S.lab;
-        for (int it = 0; it < local_sweeps; ++it) {
-            int busy = 0;
-#pragma unroll 1
-            for (int k = 0; k < kPerThread; ++k) {
-                if (!own[k]) continue;
-                const int s = threadIdx.x + kTileThreads * k;
-                const int c = s / TZ;
-                const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
-                const int e = vexc[s];
-                const int h = vlab[s];
-                if (e <= 0 || h >= POG_INF) continue;
-                busy = 1;
-                const int sk = ((volatile int *)S.snk)[s];
-                if (sk > 0) {
-                    if (h > 0) {
-                        const int d = e < sk ? e : sk;
-                        S.snk[s] = sk - d;
-                        atomicSub(&S.exc[s], d);
-                    } else {
-                        S.lab[s] = 1;
-                    }
-                    continue;
-                }
-                // gather: residual and far-end label of every arc (slots as in gather_out),
-                // every load issued before any is used
-                int res[kMaxArcs], far_lab[kMaxArcs];
-#pragma unroll
-                for (int k = 0; k < kMaxArcs; ++k) {
-                    int x2, y2, z2;
-                    res[k] = 0;
-                    far_lab[k] = POG_INF;
-                    if (!far_node(g, soft, k, x, y, z, x2, y2, z2)) continue;
-                    const Where w = where(x2, y2, z2);
-                    const int d = k >= 2 ? (k - 2) / 3 : 0;
-                    const int kind = k < 2 ? k : 2 + (k - 2) % 3;  // 0 down, 1 up, 2 hout, 3 hin, 4 soft
-                    if (kind == 0) res[k] = POG_CAP_INF - ((volatile int *)S.fdn)[s];
-                    else if (kind == 1) res[k] = w.in ? ((volatile int *)S.fdn)[w.s] : ldcg(g.fdn + w.gidx);
-                    else if (kind == 2) res[k] = POG_CAP_INF - ((volatile int *)S.fh[d])[s];
-                    else if (kind == 3) res[k] = w.in ? ((volatile int *)S.fh[d ^ 1])[w.s] : ldcg(g.fh[d ^ 1] + w.gidx);
-                    else if (d & 1) res[k] = g.alpha - ((volatile int *)SS.gs[d >> 1])[s];
-                    else res[k] = g.alpha + (w.in ? ((volatile int *)SS.gs[d >> 1])[w.s] : ldcg(g.gs[d >> 1] + w.gidx));
-                    far_lab[k] = w.in ? vlab[w.s] : ldcg(g.lab + w.gidx);
-                }
-                int best = POG_INF, bk = -1, bres = 0;
-#pragma unroll
-                for (int k = 0; k < kMaxArcs; ++k)
-                    if (res[k] > 0 && far_lab[k] < best) {
-                        best = far_lab[k];
-                        bk = k;
-                        bres = res[k];
-                    }
-                if (bk < 0 || h <= best) {  // relabel (Algorithm 2)
-                    S.lab[s] = best >= POG_INF - 1 ? POG_INF : best + 1;
-                    continue;
-                }
-                int x2, y2, z2;
-                far_node(g, soft, bk, x, y, z, x2, y2, z2);
-                const Where bw = where(x2, y2, z2);
-                const int bd = bk >= 2 ? (bk - 2) / 3 : 0;
-                const int bkind = bk < 2 ? bk : 2 + (bk - 2) % 3;
-                const int delta = e < bres ? e : bres;
-                int sat = 0;
-                switch (bkind) {
-                    case 0: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
-                    case 1:
-                        if (bw.in) atomicSub(&S.fdn[bw.s], delta);
-                        else atomicSub(g.fdn + bw.gidx, delta);
-                        break;
-                    case 2: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
-                    case 3:
-                        if (bw.in) atomicSub(&S.fh[bd ^ 1][bw.s], delta);
-                        else atomicSub(g.fh[bd ^ 1] + bw.gidx, delta);
-                        break;
-                    default:
-                        if (bd & 1) atomicAdd(&SS.gs[bd >> 1][s], delta);
-                        else if (bw.in) atomicSub(&SS.gs[bd >> 1][bw.s], delta);
-                        else atomicSub(g.gs[bd >> 1] + bw.gidx, delta);
-                        break;
-                }
-                atomicSub(&S.exc[s], delta);
-                int old;
-                if (bw.in) old = atomicAdd(&S.exc[bw.s], delta);
-                else old = atomicAdd(g.exc + bw.gidx, delta);
-                if (old > 0x7fffffff - delta) sat = 1;
-                if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
-            }
-            if (!__any_sync(0xffffffffu, busy)) break;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&b.ctr->tiles_visited, 1ull);
-
-        // ---- write back: owner-only words by store, shared words as deltas
-#pragma unroll
-        for (int k = 0; k < kPerThread; ++k) {
-            if (!own[k]) continue;
-            const int s = threadIdx.x + kTileThreads * k;
-            const int u = node[k];
-            g.lab[u] = S.lab[s];
-            g.snk[u] = S.snk[s];
-            int d = S.exc[s] - S.exc0[s];
-            if (d) atomicAdd(g.exc + u, d);
-            d = S.fdn[s] - S.fdn0[s];
-            if (d) atomicAdd(g.fdn + u, d);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                d = S.fh[j][s] - S.fh0[j][s];
-                if (d) atomicAdd(g.fh[j] + u, d);
-            }
-            if (soft) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    d = SS.gs[j][s] - SS.gs0[j][s];
-                    if (d) atomicAdd(g.gs[j] + u, d);
-                }
-            }
-        }
+        if (SINGLE) tile_visit<TX, TY, TZ, SOFT>(g0, b, tile, tile - tile_base0, flag, local_sweeps, S, SS);
+        else tile_visit<TX, TY, TZ, SOFT>(sg, b, tile, local_tile, flag, local_sweeps, S, SS);
     }
 }
 
@@ -335,35 +346,42 @@ long long tile_count_max(const Grid &g) {
     return m;
 }
 
-template <int TX, int TY, int TZ>
-cudaError_t launch_tile_kernel(const Batch &b, bool soft, int *flag, int *list, int *work, int local_sweeps,
-                               int blocks, cudaStream_t st) {
-    const size_t smem = sizeof(TileSmem) + (soft ? sizeof(TileSoft) : 0);
-    static bool configured[2] = {false, false};
-    cudaError_t e = cudaSuccess;
-    if (!configured[soft]) {
-        e = soft ? cudaFuncSetAttribute(k_tile_push_relabel<TX, TY, TZ, true>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                 : cudaFuncSetAttribute(k_tile_push_relabel<TX, TY, TZ, false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
+cudaError_t launch_tile_instance(const Batch &b, const Grid &g0, int tile_base0, int *flag, int *list, int *work,
+                                 int local_sweeps, int blocks, cudaStream_t st) {
+    const size_t smem = sizeof(TileSmem) + (SOFT ? sizeof(TileSoft) : 0);
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(k_tile_push_relabel<TX, TY, TZ, SOFT, SINGLE>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[soft] = true;
+        configured = true;
     }
-    if (soft)
-        k_tile_push_relabel<TX, TY, TZ, true><<<blocks, kTileThreads, smem, st>>>(b, list, work, flag, work + 1,
-                                                                                 local_sweeps);
-    else
-        k_tile_push_relabel<TX, TY, TZ, false><<<blocks, kTileThreads, smem, st>>>(b, list, work, flag, work + 1,
-                                                                                  local_sweeps);
+    k_tile_push_relabel<TX, TY, TZ, SOFT, SINGLE><<<blocks, kTileThreads, smem, st>>>(b, g0, tile_base0, list, work,
+                                                                                      flag, work + 1, local_sweeps);
     return cudaGetLastError();
+}
+
+template <int TX, int TY, int TZ>
+cudaError_t launch_tile_kernel(const Batch &b, const Grid *single, int single_tile_base, bool soft, int *flag,
+                               int *list, int *work, int local_sweeps, int blocks, cudaStream_t st) {
+    const Grid g0 = single ? *single : Grid{};
+    const int t0 = single_tile_base;
+    if (single)
+        return soft ? launch_tile_instance<TX, TY, TZ, true, true>(b, g0, t0, flag, list, work, local_sweeps, blocks, st)
+                    : launch_tile_instance<TX, TY, TZ, false, true>(b, g0, t0, flag, list, work, local_sweeps, blocks,
+                                                                    st);
+    return soft ? launch_tile_instance<TX, TY, TZ, true, false>(b, g0, 0, flag, list, work, local_sweeps, blocks, st)
+                : launch_tile_instance<TX, TY, TZ, false, false>(b, g0, 0, flag, list, work, local_sweeps, blocks, st);
 }
 
 // One tiled sweep over every volume of the batch: list the tiles that hold an active
 // node, then let persistent blocks take tiles from the list. `work` holds [count, next];
 // `flag` is one int per union tile and must start zeroed (visited tiles clear theirs).
-// `soft`: some volume has alpha > 0.
-cudaError_t launch_tile_sweep(const Batch &b, bool soft, int shape, int *flag, int *list, int *work,
-                              int local_sweeps, cudaStream_t st) {
+// `soft`: some volume has alpha > 0; `single`: the view of the only volume (whose tiles
+// start at union tile `single_tile_base`), or null.
+cudaError_t launch_tile_sweep(const Batch &b, const Grid *single, int single_tile_base, bool soft, int shape,
+                              int *flag, int *list, int *work, int local_sweeps, cudaStream_t st) {
     if (shape < 0 || shape >= kTileShapes) shape = 0;
     cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -372,10 +390,10 @@ cudaError_t launch_tile_sweep(const Batch &b, bool soft, int shape, int *flag, i
     k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag, list, work);
     const int blocks = sms * 3;
     switch (shape) {
-        case 1: return launch_tile_kernel<8, 8, 16>(b, soft, flag, list, work, local_sweeps, blocks, st);
-        case 2: return launch_tile_kernel<4, 4, 64>(b, soft, flag, list, work, local_sweeps, blocks, st);
-        case 3: return launch_tile_kernel<2, 4, 128>(b, soft, flag, list, work, local_sweeps, blocks, st);
-        default: return launch_tile_kernel<4, 8, 32>(b, soft, flag, list, work, local_sweeps, blocks, st);
+        case 1: return launch_tile_kernel<8, 8, 16>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
+        case 2: return launch_tile_kernel<4, 4, 64>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
+        case 3: return launch_tile_kernel<2, 4, 128>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
+        default: return launch_tile_kernel<4, 8, 32>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
     }
 }
 

@@ -214,3 +214,22 @@ def test_batch_uneven():
         ref = oracle.solve(c, v.delta, v.alpha)
         assert f == ref.flow
         np.testing.assert_array_equal(h.cpu().numpy(), ref.heights)
+
+
+def test_batch_last_live_volume_is_not_the_first():
+    """Small easy volumes finish first; the hard one that finishes last sits at a nonzero
+    node and tile offset (the single-volume kernels then run on a slice of the union)."""
+    rng = np.random.default_rng(51)
+    easy = [np.sort(rng.integers(0, 50, size=(9, 7, 20)), axis=2).astype(np.int32) for _ in range(3)]
+    hard = synth.horizon_cost(synth.scaled_spec(70, 40, 96, 99, stream=61))
+    costs = easy[:2] + [hard] + easy[2:]
+    deltas = [1, 2, 3, 1]
+    alphas = [0, 5, 20, 0]
+    opts = pog.make_options(max_rounds=5000)
+    for shape in (0, 1):
+        opts.tile_shape = shape
+        flows, hs = pog.pog_solve_batch([torch.from_numpy(c).cuda() for c in costs], deltas, alphas, opts)
+        for c, d, a, f, h in zip(costs, deltas, alphas, flows, hs):
+            ref = oracle.solve(c, d, a)
+            assert f == ref.flow
+            np.testing.assert_array_equal(h.cpu().numpy(), ref.heights)
