@@ -238,12 +238,30 @@ typedef struct {
 } pog_volume;
 
 /*
- * Solve n independent volumes (sizes may differ). flows_out: host int64 [n];
- * heights_dev[i]: device int32 [X_i][Y_i]. Blocks until done. The first failing
- * volume's status is returned; flows of the others are still written.
+ * Solve n independent volumes (sizes may differ) as one batch: the disjoint union of
+ * their graphs goes through the same launches (one global relabel, one tiled sweep, one
+ * cut extraction for all of them), and volumes leave the work once their relabel finds
+ * no active node. flows_out: host int64 [n]; heights_dev[i]: device int32 [X_i][Y_i].
+ * Blocks until done. At most 1024 volumes, fewer than 2^31 nodes in all.
  */
 POG_API pog_status pog_solve_batch(int32_t n, const pog_volume *vols, const pog_options *opt,
                            void *stream, int64_t *flows_out, int32_t *const *heights_dev);
+
+/*
+ * Solve B float32 volumes of one shape as one batch (the differentiable path): each is
+ * quantised on the fly to round_half_even(scale * c), optionally with `margin` added at
+ * node (x, y, h_aug[b][x][y]) as in pog_build_f32_augmented.
+ *   cost_dev     : device float32 [B][X][Y][Z].
+ *   h_aug_dev    : device int32 [B][X][Y], or NULL for no augmentation.
+ *   flows_out    : host int64 [B], max-flow values.
+ *   energies_out : host int64 [B] or NULL, optimal energies E*(h) (as pog_energy).
+ *   heights_dev  : device int32 [B][X][Y], the surfaces.
+ * Blocks until done.
+ */
+POG_API pog_status pog_solve_batch_f32(int32_t B, const float *cost_dev, float scale, const int32_t *h_aug_dev,
+                                       int32_t margin, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                                       int32_t alpha, const pog_options *opt, void *stream, int64_t *flows_out,
+                                       int64_t *energies_out, int32_t *heights_dev);
 
 /*
  * Solve one volume without allocating anything (the paper has no counterpart; this

@@ -7,4 +7,4 @@
 """
 from .pog import (PogError, make_options, pog_backward, pog_build, pog_build_f32,  # noqa: F401
                   pog_build_f32_augmented, pog_energy, pog_export_state, pog_free, pog_maxflow, pog_quantise,
-                  pog_solve_batch, pog_stats, pog_strerror, pog_surface, pog_surface_energy, solve)
+                  pog_solve_batch, pog_solve_batch_f32, pog_stats, pog_strerror, pog_surface, pog_surface_energy, solve)

@@ -28,18 +28,8 @@ def _alpha_q(alpha: float, scale: float) -> int:
 
 
 def _solve_all(cost, delta, alpha_q, scale, options, h_aug=None, margin_q=0):
-    B, X, Y, Z = cost.shape
-    heights = torch.empty((B, X, Y), dtype=torch.int32, device=cost.device)
-    energies = []
-    for b in range(B):
-        if h_aug is None:
-            g = pog.pog_build_f32(cost[b], scale, delta, alpha_q, options)
-        else:
-            g = pog.pog_build_f32_augmented(cost[b], scale, h_aug[b], margin_q, delta, alpha_q, options)
-        with g:
-            pog.pog_maxflow(g)
-            pog.pog_surface(g, heights[b])
-            energies.append(pog.pog_energy(g))
+    """All volumes of the batch in one batched solve (quantisation fused into the build)."""
+    _, energies, heights = pog.pog_solve_batch_f32(cost, scale, delta, alpha_q, h_aug, margin_q, options)
     return heights, torch.tensor(energies, dtype=torch.int64)
 
 

@@ -222,9 +222,12 @@ pog_status maxflow_impl(pog_graph *g) {
             POG_TRY_CUDA(timed(g, TM_SWEEP, [&] {
                 if (g->flags & POG_FLAG_NODE_SWEEPS)
                     return pog::launch_sweep(g->live, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
-                return pog::launch_tile_sweep(g->live, g->nlive == 1 ? &g->live_vols[0] : nullptr,
-                                              g->live_tile_base[0], g->any_soft, g->tile_shape, g->tile_flag,
-                                              g->tile_list, g->tile_work, g->tile_sweeps, g->stream);
+                const cudaError_t e = pog::launch_tile_sweep(
+                    g->live, g->nlive == 1 ? &g->live_vols[0] : nullptr, g->live_tile_base[0], g->any_soft,
+                    g->tile_shape, g->tiles, g->ntiles, g->tile_work, g->tile_parity, k == 0, g->tile_sweeps,
+                    g->stream);
+                g->tile_parity ^= 1;
+                return e;
             }));
             if (gap && k + 1 == half) {
                 POG_TRY(reset_field(g, &DevCounters::raised));
@@ -344,7 +347,7 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
     const size_t tile_bytes = align_up(sizeof(int32_t) * (size_t)tiles, 256);
     const size_t table = 2 * (align_up(sizeof(Grid) * n, 256) + 2 * align_up(sizeof(int) * (n + 1), 256));
-    g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 2 * tile_bytes + 256 + table;
+    g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 4 * tile_bytes + 256 + table;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -381,8 +384,9 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->heights = reinterpret_cast<int32_t *>(take(heights));
     g->bfs_sync = reinterpret_cast<pog::BfsSync *>(take(sync));
     g->trace = reinterpret_cast<pog::LevelTrace *>(take(trace));
-    g->tile_flag = reinterpret_cast<int32_t *>(take(tile_bytes));
-    g->tile_list = reinterpret_cast<int32_t *>(take(tile_bytes));
+    g->tiles = reinterpret_cast<int32_t *>(take(4 * tile_bytes));
+    g->ntiles = (long long)(tile_bytes / sizeof(int32_t));
+    g->tile_parity = 0;
     g->tile_work = reinterpret_cast<int32_t *>(take(256));
     g->vctr = reinterpret_cast<DevCounters *>(take(vctr));
     g->vols_dev = reinterpret_cast<Grid *>(take(align_up(sizeof(Grid) * n, 256)));
@@ -427,7 +431,8 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
         e = cudaMemcpyAsync(g->tile_base_dev, g->tile_base, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->vctr, 0, sizeof(DevCounters) * n, g->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_flag, 0, tile_bytes, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->tiles, 0, 4 * tile_bytes, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_work, 0, 4 * sizeof(int32_t), g->stream);
     for (int v = 0; v < n && e == cudaSuccess; ++v)
         e = timed(g, TM_BUILD, [&] { return launch(v, g->vols[v], g->stream); });
     if (e != cudaSuccess) {
@@ -670,6 +675,42 @@ pog_status pog_solve_batch(int32_t n, const pog_volume *vols, const pog_options 
                                           sizeof(int32_t) * (size_t)vols[i].X * vols[i].Y, cudaMemcpyDeviceToDevice,
                                           g->stream));
         }
+    }
+    pog_free(g);  // synchronises the stream first
+    return s;
+}
+
+pog_status pog_solve_batch_f32(int32_t B, const float *cost_dev, float scale, const int32_t *h_aug_dev,
+                               int32_t margin, int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha,
+                               const pog_options *opt, void *stream, int64_t *flows_out, int64_t *energies_out,
+                               int32_t *heights_dev) {
+    if (B < 0 || (B > 0 && (!cost_dev || !flows_out || !heights_dev)) || !(scale > 0.0f)) return POG_E_INVALID;
+    if (h_aug_dev && (margin < 0 || margin >= (1 << 28))) return POG_E_INVALID;
+    if (B == 0) return POG_OK;
+    if (B > pog::kMaxVolumes) return POG_E_INVALID;
+    VolumeSpec *spec = new (std::nothrow) VolumeSpec[B];
+    if (!spec) return POG_E_NOMEM;
+    for (int i = 0; i < B; ++i) spec[i] = VolumeSpec{X, Y, Z, delta, alpha};
+    const size_t vol = (size_t)X * Y * Z, cols = (size_t)X * Y;
+    pog_graph *g = nullptr;
+    pog_status s = build_batch(B, spec, opt, stream, &g, [&](int v, const Grid &gr, cudaStream_t st) {
+        return pog::launch_build_f32(gr, cost_dev + v * vol, scale, h_aug_dev ? h_aug_dev + v * cols : nullptr,
+                                     h_aug_dev ? margin : 0, st);
+    });
+    delete[] spec;
+    if (s != POG_OK) return s;
+    s = maxflow_impl(g);
+    if (s == POG_OK) {
+        for (int i = 0; i < B; ++i) {
+            flows_out[i] = g->flows[i];
+            if (energies_out) {
+                const DevCounters &c = volume_counters(g, i);
+                const long long K = -1 - (long long)c.bottom_sum + (long long)c.src_total + (long long)c.neg_bottom;
+                energies_out[i] = g->flows[i] - K;
+            }
+        }
+        s = from_cuda(cudaMemcpyAsync(heights_dev, g->heights, sizeof(int32_t) * cols * B, cudaMemcpyDeviceToDevice,
+                                      g->stream));
     }
     pog_free(g);  // synchronises the stream first
     return s;

@@ -253,9 +253,10 @@ struct pog_graph {
     int32_t *queue_a, *queue_b;  // device [n_total] each: BFS frontiers
     pog::BfsSync *bfs_sync;      // device: grid barrier + frontier sizes
     pog::LevelTrace *trace;      // device [kTraceLevels]: last global relabel
-    int32_t *tile_flag;          // device [tiles]: listed in the current tiled sweep
-    int32_t *tile_list;          // device [tiles]
-    int32_t *tile_work;          // device [2]: listed tiles, next tile to take
+    int32_t *tiles;              // device [4][ntiles]: flag and list of two alternating sweep lists
+    long long ntiles;
+    int32_t *tile_work;          // device [4]: per list, listed tiles and next tile to take
+    int tile_parity;             // list the next tiled sweep visits
     pog::DevCounters *ctr;       // device: union counters
     pog::DevCounters *vctr;      // device [nvol]: per-volume counters
     pog::DevCounters *ctr_host;  // pinned host mirror of ctr followed by vctr

@@ -77,7 +77,7 @@ size_t scratch_bytes(int X, int Y, int Z, int alpha) {
     dims.Y = Y;
     dims.Z = Z;
     const size_t tiles = (size_t)pog::tile_count_max(dims);
-    return (arrays + 2) * align_up(N * 4, 256) + 2 * align_up(tiles * 4, 256) + 256 +
+    return (arrays + 2) * align_up(N * 4, 256) + align_up(4 * tiles * 4, 256) + 256 +
            align_up(sizeof(pog::BfsSync), 256) + 2 * align_up(sizeof(pog::DevCounters), 256) + kGapLevels / 8 +
            align_up(sizeof(pog::Grid), 256) + 2 * 256;
 }
@@ -134,8 +134,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     const size_t tiles = (size_t)pog::tile_count_max(g);
     const int shape = (opt && opt->tile_shape > 0 && opt->tile_shape < pog::kTileShapes) ? opt->tile_shape : 0;
     const int bu_ratio = !opt || opt->bfs_bottom_up_ratio == 0 ? 8 : (opt->bfs_bottom_up_ratio < 0 ? 0 : opt->bfs_bottom_up_ratio);
-    int32_t *tile_flag = c.take<int32_t>(tiles * 4);
-    int32_t *tile_list = c.take<int32_t>(tiles * 4);
+    int32_t *tile_lists = c.take<int32_t>(4 * tiles * 4);
     int32_t *tile_work = c.take<int32_t>(256);
     pog::BfsSync *sync = c.take<pog::BfsSync>(sizeof(pog::BfsSync));
     pog::DevCounters *uctr = c.take<pog::DevCounters>(sizeof(pog::DevCounters));
@@ -162,7 +161,8 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     NA_TRY_CUDA(cudaMemcpyAsync(tile_base, tbases, sizeof(tbases), cudaMemcpyHostToDevice, st));
     NA_TRY_CUDA(cudaMemsetAsync(uctr, 0, sizeof(pog::DevCounters), st));
     NA_TRY_CUDA(cudaMemsetAsync(g.ctr, 0, sizeof(pog::DevCounters), st));
-    NA_TRY_CUDA(cudaMemsetAsync(tile_flag, 0, tiles * 4, st));
+    NA_TRY_CUDA(cudaMemsetAsync(tile_lists, 0, 4 * tiles * 4, st));
+    NA_TRY_CUDA(cudaMemsetAsync(tile_work, 0, 4 * sizeof(int32_t), st));
     NA_TRY_CUDA(pog::launch_build_i32(g, cost_dev, st));
 
     pog::DevCounters host[2];
@@ -170,6 +170,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     NA_TRY(read_counters(uctr, g.ctr, host, st));
     if (!(flags & POG_FLAG_NO_PREPUSH)) NA_TRY_CUDA(pog::launch_column_prepush(g, st));
     const bool soft = alpha > 0;
+    int parity = 0;
     for (int round = 0;; ++round) {
         NA_TRY_CUDA(cudaMemsetAsync(&uctr->active, 0, sizeof(host[0].active), st));
         NA_TRY_CUDA(pog::launch_global_relabel(b, &g, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
@@ -180,8 +181,9 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
             if (flags & POG_FLAG_NODE_SWEEPS)
                 NA_TRY_CUDA(pog::launch_sweep(b, queue_a, &sync->size[0], kNodeOps, st));
             else
-                NA_TRY_CUDA(pog::launch_tile_sweep(b, &g, 0, soft, shape, tile_flag, tile_list, tile_work,
-                                                   tile_sweeps, st));
+                NA_TRY_CUDA(pog::launch_tile_sweep(b, &g, 0, soft, shape, tile_lists, (long long)tiles, tile_work,
+                                                   parity, k == 0, tile_sweeps, st));
+            parity ^= 1;
             if (!(flags & POG_FLAG_NO_GAP) && k + 1 == sweeps / 2) {
                 NA_TRY_CUDA(cudaMemsetAsync(&uctr->max_label, 0, sizeof(int), st));
                 NA_TRY_CUDA(pog::launch_gap(b, gap_bits, kGapLevels, st));

@@ -40,7 +40,14 @@ TileGeom geom(const Grid &g, int shape) {
                     (g.Z + sh[2] - 1) / sh[2]};
 }
 
-// List every tile (union numbering) that holds an active node, once.
+// Append tile t to a list once (its flag guards the membership).
+__device__ __forceinline__ void list_tile(int t, int *flag, int *list, int *count) {
+    if (__ldcg(flag + t)) return;
+    if (atomicExch(flag + t, 1) == 0) list[atomicAdd(count, 1)] = t;
+}
+
+// List every tile (union numbering) that holds an active node, once. Each thread keeps
+// four independent excess loads in flight.
 __global__ void __launch_bounds__(256) k_collect_tiles(Batch b, int tx, int ty, int tz, int *flag, int *list,
                                                        int *count) {
     const int stride = gridDim.x * blockDim.x;
@@ -48,14 +55,22 @@ __global__ void __launch_bounds__(256) k_collect_tiles(Batch b, int tx, int ty, 
         const Grid g = b.vols[vi];
         const int tbase = b.tile_base[vi];
         const int nty = (g.Y + ty - 1) / ty, ntz = (g.Z + tz - 1) / tz;
-        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.N; u += stride) {
-            if (__ldcg(g.exc + u) <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
-            const int z = u % g.Z;
-            const int col = u / g.Z;
-            const int x = col / g.Y, y = col - x * g.Y;
-            const int tile = tbase + ((x / tx) * nty + (y / ty)) * ntz + z / tz;
-            if (__ldcg(flag + tile)) continue;
-            if (atomicExch(flag + tile, 1) == 0) list[atomicAdd(count, 1)] = tile;
+        for (int u0 = blockIdx.x * blockDim.x + threadIdx.x; u0 < g.N; u0 += 4 * stride) {
+            int e[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = u0 + j * stride;
+                e[j] = u < g.N ? __ldcg(g.exc + u) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = u0 + j * stride;
+                if (e[j] <= 0 || u % g.Z == 0 || __ldcg(g.lab + u) >= POG_INF) continue;
+                const int z = u % g.Z;
+                const int col = u / g.Z;
+                const int x = col / g.Y, y = col - x * g.Y;
+                list_tile(tbase + ((x / tx) * nty + (y / ty)) * ntz + z / tz, flag, list, count);
+            }
         }
     }
 }
@@ -91,6 +106,12 @@ __device__ __forceinline__ bool far_node(const Grid &g, bool soft, int k, int x,
     return soft;
 }
 
+// Unlist the tiles of one list (clear their flags) and empty it.
+__global__ void __launch_bounds__(256) k_clear_listed(int *flag, const int *list, int *count) {
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flag[list[i]] = 0;
+}
+
 // Shared-memory image of a tile: current values and the values at load time (for the
 // delta write-back). Arrays are indexed by the node's place s in the tile.
 struct TileSmem {
@@ -98,6 +119,7 @@ struct TileSmem {
     int fh[4][kTileNodes];
     int exc0[kTileNodes], fdn0[kTileNodes];
     int fh0[4][kTileNodes];
+    unsigned nb;  // neighbour tiles pushed into: bit (dx+1)*9 + (dy+1)*3 + (dz+1)
 };
 struct TileSoft {
     int gs[2][kTileNodes];
@@ -110,18 +132,33 @@ struct Where {
     int gidx;  // global node index
 };
 
+// Lists of a tiled sweep: the tiles to visit now, and the next sweep's tiles (those a
+// visit leaves active, and those that receive a push across their boundary).
+struct TileLists {
+    const int *list;  // this sweep's tiles
+    const int *count;
+    int *flag;        // membership in this sweep's list (cleared by each visit)
+    int *next;        // work counter of this sweep
+    int *nlist;       // next sweep's tiles
+    int *ncount;
+    int *nflag;
+};
+
 // One visit of one tile: stage it in shared memory, run the local sweeps, write it back.
-// `g` is the tile's volume, `tile` its union index (for the listing flag), `local_tile`
+// `g` is the tile's volume, `tile` its union index (for the listing flags), `local_tile`
 // its index within the volume.
 template <int TX, int TY, int TZ, bool SOFT>
-__device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int tile, int local_tile, int *flag,
-                                           int local_sweeps, TileSmem &S, TileSoft &SS) {
+__device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int tile, int local_tile,
+                                           const TileLists &L, int local_sweeps, TileSmem &S, TileSoft &SS) {
     const bool soft = SOFT && g.gs[0] != nullptr;
     const int nty = (g.Y + TY - 1) / TY, ntz = (g.Z + TZ - 1) / TZ;
     const int tz = local_tile % ntz;
     const int txy = local_tile / ntz;
     const int x0 = (txy / nty) * TX, y0 = (txy % nty) * TY, z0 = tz * TZ;
-    if (threadIdx.x == 0) flag[tile] = 0;  // the tile may be listed again by a later scan
+    if (threadIdx.x == 0) {
+        L.flag[tile] = 0;  // this sweep's listing is consumed
+        S.nb = 0;
+    }
 
     // ---- load (coalesced along z)
     int node[kPerThread];
@@ -258,10 +295,33 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
             else old = atomicAdd(g.exc + bw.gidx, delta);
             if (old > 0x7fffffff - delta) sat = 1;
             if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
+            if (!bw.in) {  // the receiving tile has work next sweep
+                const int dz = z2 < z0 ? 0 : (z2 < z0 + TZ ? 1 : 2);
+                if (z2 >= z0 - TZ && z2 < z0 + 2 * TZ) {
+                    const int dx = x2 < x0 ? 0 : (x2 < x0 + TX ? 1 : 2);
+                    const int dy = y2 < y0 ? 0 : (y2 < y0 + TY ? 1 : 2);
+                    atomicOr(&S.nb, 1u << (dx * 9 + dy * 3 + dz));
+                } else {  // a vertical offset longer than a tile
+                    list_tile(tile - local_tile + ((x2 / TX) * nty + (y2 / TY)) * ntz + z2 / TZ, L.nflag, L.nlist,
+                              L.ncount);
+                }
+            }
         }
         if (!__any_sync(0xffffffffu, busy)) break;
     }
     __syncthreads();
+    int still = 0;  // does the tile keep an active node for the next sweep?
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+        const int s = threadIdx.x + kTileThreads * k;
+        still |= own[k] && S.exc[s] > 0 && S.lab[s] < POG_INF;
+    }
+    const unsigned keep = __syncthreads_or(still) ? 1u << 13 : 0u;  // bit 13, (dx, dy, dz) = 0: this tile
+    if (threadIdx.x < 27 && (((S.nb | keep) >> threadIdx.x) & 1u)) {
+        const int t = threadIdx.x;
+        const int nx = txy / nty + t / 9 - 1, ny = txy % nty + (t / 3) % 3 - 1, nz = tz + t % 3 - 1;
+        list_tile(tile - local_tile + (nx * nty + ny) * ntz + nz, L.nflag, L.nlist, L.ncount);
+    }
     if (threadIdx.x == 0) atomicAdd(&b.ctr->tiles_visited, 1ull);
 
     // ---- write back: owner-only words by store, shared words as deltas
@@ -295,20 +355,19 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
 // whether a given tile uses them is decided per volume. SINGLE: a batch of one volume,
 // whose view comes in as a kernel parameter (read from the constant bank).
 template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
-__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, Grid g0, int tile_base0,
-                                                                    const int *list, const int *count, int *flag,
-                                                                    int *next, int local_sweeps) {
+__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, Grid g0, int tile_base0, TileLists L,
+                                                                    int local_sweeps) {
     extern __shared__ int4 smem_raw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
     TileSoft &SS = *reinterpret_cast<TileSoft *>(reinterpret_cast<char *>(smem_raw) + sizeof(TileSmem));
     __shared__ int tile_id, local_tile;
     __shared__ Grid sg;
-    const int ntiles = *count;
+    const int ntiles = *L.count;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int slot = atomicAdd(next, 1);
-            tile_id = slot < ntiles ? list[slot] : -1;
+            const int slot = atomicAdd(L.next, 1);
+            tile_id = slot < ntiles ? L.list[slot] : -1;
             if (!SINGLE && tile_id >= 0) {
                 const int vi = find_volume(b.tile_base, b.nvol, tile_id);
                 sg = b.vols[vi];
@@ -318,8 +377,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, 
         __syncthreads();
         const int tile = tile_id;
         if (tile < 0) return;
-        if (SINGLE) tile_visit<TX, TY, TZ, SOFT>(g0, b, tile, tile - tile_base0, flag, local_sweeps, S, SS);
-        else tile_visit<TX, TY, TZ, SOFT>(sg, b, tile, local_tile, flag, local_sweeps, S, SS);
+        if (SINGLE) tile_visit<TX, TY, TZ, SOFT>(g0, b, tile, tile - tile_base0, L, local_sweeps, S, SS);
+        else tile_visit<TX, TY, TZ, SOFT>(sg, b, tile, local_tile, L, local_sweeps, S, SS);
     }
 }
 
@@ -347,8 +406,8 @@ long long tile_count_max(const Grid &g) {
 }
 
 template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
-cudaError_t launch_tile_instance(const Batch &b, const Grid &g0, int tile_base0, int *flag, int *list, int *work,
-                                 int local_sweeps, int blocks, cudaStream_t st) {
+cudaError_t launch_tile_instance(const Batch &b, const Grid &g0, int tile_base0, const TileLists &L, int local_sweeps,
+                                 int blocks, cudaStream_t st) {
     const size_t smem = sizeof(TileSmem) + (SOFT ? sizeof(TileSoft) : 0);
     static bool configured = false;
     if (!configured) {
@@ -357,43 +416,58 @@ cudaError_t launch_tile_instance(const Batch &b, const Grid &g0, int tile_base0,
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_tile_push_relabel<TX, TY, TZ, SOFT, SINGLE><<<blocks, kTileThreads, smem, st>>>(b, g0, tile_base0, list, work,
-                                                                                      flag, work + 1, local_sweeps);
+    k_tile_push_relabel<TX, TY, TZ, SOFT, SINGLE><<<blocks, kTileThreads, smem, st>>>(b, g0, tile_base0, L,
+                                                                                      local_sweeps);
     return cudaGetLastError();
 }
 
 template <int TX, int TY, int TZ>
-cudaError_t launch_tile_kernel(const Batch &b, const Grid *single, int single_tile_base, bool soft, int *flag,
-                               int *list, int *work, int local_sweeps, int blocks, cudaStream_t st) {
+cudaError_t launch_tile_kernel(const Batch &b, const Grid *single, int single_tile_base, bool soft,
+                               const TileLists &L, int local_sweeps, int blocks, cudaStream_t st) {
     const Grid g0 = single ? *single : Grid{};
     const int t0 = single_tile_base;
     if (single)
-        return soft ? launch_tile_instance<TX, TY, TZ, true, true>(b, g0, t0, flag, list, work, local_sweeps, blocks, st)
-                    : launch_tile_instance<TX, TY, TZ, false, true>(b, g0, t0, flag, list, work, local_sweeps, blocks,
-                                                                    st);
-    return soft ? launch_tile_instance<TX, TY, TZ, true, false>(b, g0, 0, flag, list, work, local_sweeps, blocks, st)
-                : launch_tile_instance<TX, TY, TZ, false, false>(b, g0, 0, flag, list, work, local_sweeps, blocks, st);
+        return soft ? launch_tile_instance<TX, TY, TZ, true, true>(b, g0, t0, L, local_sweeps, blocks, st)
+                    : launch_tile_instance<TX, TY, TZ, false, true>(b, g0, t0, L, local_sweeps, blocks, st);
+    return soft ? launch_tile_instance<TX, TY, TZ, true, false>(b, g0, 0, L, local_sweeps, blocks, st)
+                : launch_tile_instance<TX, TY, TZ, false, false>(b, g0, 0, L, local_sweeps, blocks, st);
 }
 
-// One tiled sweep over every volume of the batch: list the tiles that hold an active
-// node, then let persistent blocks take tiles from the list. `work` holds [count, next];
-// `flag` is one int per union tile and must start zeroed (visited tiles clear theirs).
-// `soft`: some volume has alpha > 0; `single`: the view of the only volume (whose tiles
-// start at union tile `single_tile_base`), or null.
+// The tile lists of a sweep alternate between two buffers. Buffer p's tiles are visited;
+// visits list the next sweep's tiles in buffer 1-p (whose flags are all clear: every
+// visit clears its own flag in p). After a global relabel, activity is recomputed, and
+// volumes may have left the batch, so the first sweep of a round (`full_scan`) drops
+// buffer p's carried list and scans every node of the batch into it.
+// `tiles` holds [flag p][list p] for p = 0, 1 (4 arrays of `ntiles`); `work` holds
+// [count, next] per buffer. `soft`: some volume has alpha > 0; `single`: the view of the
+// only volume (whose tiles start at union tile `single_tile_base`), or null.
 cudaError_t launch_tile_sweep(const Batch &b, const Grid *single, int single_tile_base, bool soft, int shape,
-                              int *flag, int *list, int *work, int local_sweeps, cudaStream_t st) {
+                              int *tiles, long long ntiles, int *work, int parity, bool full_scan, int local_sweeps,
+                              cudaStream_t st) {
     if (shape < 0 || shape >= kTileShapes) shape = 0;
-    cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(int), st);
-    if (e != cudaSuccess) return e;
+    const int p = parity & 1, q = p ^ 1;
+    int *flag[2] = {tiles, tiles + 2 * ntiles};
+    int *list[2] = {tiles + ntiles, tiles + 3 * ntiles};
+    int *cnt[2] = {work, work + 2};
     const int sms = sm_count();
     const int *sh = kShapes[shape];
-    k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag, list, work);
+    cudaError_t e = cudaSuccess;
+    if (full_scan) {
+        k_clear_listed<<<sms, 256, 0, st>>>(flag[p], list[p], cnt[p]);
+        e = cudaMemsetAsync(cnt[p], 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag[p], list[p], cnt[p]);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt[q], 0, 2 * sizeof(int), st);  // next list starts empty
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt[p] + 1, 0, sizeof(int), st);  // take from slot 0
+    if (e != cudaSuccess) return e;
+    TileLists L{list[p], cnt[p], flag[p], cnt[p] + 1, list[q], cnt[q], flag[q]};
     const int blocks = sms * 3;
     switch (shape) {
-        case 1: return launch_tile_kernel<8, 8, 16>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
-        case 2: return launch_tile_kernel<4, 4, 64>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
-        case 3: return launch_tile_kernel<2, 4, 128>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
-        default: return launch_tile_kernel<4, 8, 32>(b, single, single_tile_base, soft, flag, list, work, local_sweeps, blocks, st);
+        case 1: return launch_tile_kernel<8, 8, 16>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);
+        case 2: return launch_tile_kernel<4, 4, 64>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);
+        case 3: return launch_tile_kernel<2, 4, 128>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);
+        default: return launch_tile_kernel<4, 8, 32>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);
     }
 }
 

@@ -31,7 +31,7 @@ POG_FLAG_NODE_SWEEPS = 8
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
-            "pog_surface_energy", "pog_solve_batch", "pog_solve_noalloc"]
+            "pog_surface_energy", "pog_solve_batch", "pog_solve_batch_f32", "pog_solve_noalloc"]
 
 
 class PogError(RuntimeError):
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
             "pog_backward": [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp],
             "pog_solve_batch": [i32, ctypes.POINTER(pog_volume), opts, vp, i64p, ctypes.POINTER(vp)],
             "pog_solve_noalloc": [vp, i32, i32, i32, i32, i32, opts, vp, i64p, vp],
+            "pog_solve_batch_f32": [i32, vp, f32, vp, i32, i32, i32, i32, i32, i32, opts, vp, i64p, i64p, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -321,6 +322,23 @@ def pog_solve_batch(costs, deltas, alphas, options: pog_options | None = None, s
     _check(load().pog_solve_batch(n, vols, ctypes.byref(options) if options else None, _stream(stream), flows,
                                   hptrs), "pog_solve_batch")
     return [int(flows[i]) for i in range(n)], heights
+
+
+def pog_solve_batch_f32(cost, scale: float, delta: int, alpha: int, h_aug=None, margin: int = 0,
+                        options: pog_options | None = None, stream=None):
+    """float32 CUDA [B, X, Y, Z] -> (flows list, energies list, heights int32 CUDA [B, X, Y])."""
+    import torch
+
+    B, X, Y, Z = cost.shape
+    heights = torch.empty((B, X, Y), dtype=torch.int32, device=cost.device)
+    flows = (ctypes.c_int64 * max(B, 1))()
+    energies = (ctypes.c_int64 * max(B, 1))()
+    _check(load().pog_solve_batch_f32(B, _dev(cost, torch.float32, "cost"), float(scale),
+                                      None if h_aug is None else _dev(h_aug, torch.int32, "h_aug"), int(margin),
+                                      X, Y, Z, int(delta), int(alpha), ctypes.byref(options) if options else None,
+                                      _stream(stream), flows, energies, _dev(heights, torch.int32, "heights")),
+           "pog_solve_batch_f32")
+    return [int(flows[i]) for i in range(B)], [int(energies[i]) for i in range(B)], heights
 
 
 def pog_solve_noalloc(cost, delta: int, alpha: int, heights, options: pog_options | None = None, stream=None) -> int:
