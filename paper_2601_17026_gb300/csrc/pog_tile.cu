@@ -75,37 +75,6 @@ __global__ void __launch_bounds__(256) k_collect_tiles(Batch b, int tx, int ty, 
     }
 }
 
-// Far end of arc slot k of node (x, y, z) (slots as in gather_out: 0 down, 1 up, then per
-// direction d: 2+3d hard out, 3+3d reverse of the neighbour's hard arc, 4+3d soft);
-// false when the arc does not exist (soft arcs exist only when `soft`).
-__device__ __forceinline__ bool far_node(const Grid &g, bool soft, int k, int x, int y, int z, int &x2, int &y2,
-                                         int &z2) {
-    x2 = x;
-    y2 = y;
-    if (k == 0) {
-        z2 = z - 1;
-        return z >= 2;
-    }
-    if (k == 1) {
-        z2 = z + 1;
-        return z + 1 < g.Z;
-    }
-    const int d = (k - 2) / 3, kind = (k - 2) % 3;
-    x2 = x + (d == 0 ? -1 : d == 1 ? 1 : 0);
-    y2 = y + (d == 2 ? -1 : d == 3 ? 1 : 0);
-    if (x2 < 0 || x2 >= g.X || y2 < 0 || y2 >= g.Y) return false;
-    if (kind == 0) {
-        z2 = z - g.delta;
-        return z2 >= 1;
-    }
-    if (kind == 1) {
-        z2 = z + g.delta;
-        return z2 < g.Z;
-    }
-    z2 = z;
-    return soft;
-}
-
 // Unlist the tiles of one list (clear their flags) and empty it.
 __global__ void __launch_bounds__(256) k_clear_listed(int *flag, const int *list, int *count) {
     const int n = *count;
@@ -124,12 +93,6 @@ struct TileSmem {
 struct TileSoft {
     int gs[2][kTileNodes];
     int gs0[2][kTileNodes];
-};
-
-struct Where {
-    bool in;   // the far node / stored slot lies in this tile
-    int s;     // shared index when in
-    int gidx;  // global node index
 };
 
 // Lists of a tiled sweep: the tiles to visit now, and the next sweep's tiles (those a
@@ -196,32 +159,64 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
     }
     __syncthreads();
 
-    // locate node (x, y, z) relative to the tile
-    auto where = [&](int x, int y, int z) {
-        Where w;
-        w.gidx = (x * g.Y + y) * g.Z + z;
-        w.in = x >= x0 && x < x0 + TX && y >= y0 && y < y0 + TY && z >= z0 && z < z0 + TZ;
-        w.s = ((x - x0) * TY + (y - y0)) * TZ + (z - z0);
-        return w;
-    };
-
     // ---- local sweeps. Warps run them without block barriers (shared atomics keep
-    // the tile consistent, and volatile reads see other warps' progress); a warp stops
-    // early once none of its nodes is active.
+    // the tile consistent, and volatile reads see other warps' progress). In each sweep a
+    // warp gathers its active nodes with ballots and steps them 32 at a time, so a sweep
+    // costs in proportion to the active nodes; a warp stops once none of its nodes is
+    // active. Arc slots: 0 down, 1 up, then per direction d (-x, +x, -y, +y): 2+3d the
+    // hard arc out, 3+3d the reverse of the neighbour's hard arc, 4+3d the soft arc.
     volatile int *vexc = S.exc;
     volatile int *vlab = S.lab;
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const int X = g.X, Y = g.Y, Z = g.Z, D = g.delta;
+    const int sx = Y * Z;
     for (int it = 0; it < local_sweeps; ++it) {
-        int busy = 0;
-#pragma unroll 1
+        unsigned m[kPerThread];
+        int total = 0;
+#pragma unroll
         for (int k = 0; k < kPerThread; ++k) {
-            if (!own[k]) continue;
             const int s = threadIdx.x + kTileThreads * k;
-            const int c = s / TZ;
-            const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
+            m[k] = __ballot_sync(0xffffffffu, vexc[s] > 0 && vlab[s] < POG_INF);
+            total += __popc(m[k]);
+        }
+        if (total == 0) break;
+        for (int base = 0; base < total; base += 32) {
+            // the r-th active node of the warp: its row k, then its lane (binary search)
+            int r = base + lane;
+            if (r >= total) continue;
+            int k = 0;
+            unsigned v = m[0];
+            bool found = false;
+#pragma unroll
+            for (int j = 0; j < kPerThread; ++j) {
+                const int cj = __popc(m[j]);
+                if (!found) {
+                    if (r < cj) {
+                        k = j;
+                        v = m[j];
+                        found = true;
+                    } else {
+                        r -= cj;
+                    }
+                }
+            }
+            int pos = 0;
+#pragma unroll
+            for (int w = 16; w >= 1; w >>= 1) {
+                const int c = __popc(v & ((1u << w) - 1u));
+                if (r >= c) {
+                    r -= c;
+                    v >>= w;
+                    pos += w;
+                }
+            }
+            const int s = wbase + pos + kTileThreads * k;
+            const int cz = s % TZ, col = s / TZ, cy = col % TY, cx = col / TY;
+            const int x = x0 + cx, y = y0 + cy, z = z0 + cz;
+            const int u = (x * Y + y) * Z + z;
             const int e = vexc[s];
             const int h = vlab[s];
             if (e <= 0 || h >= POG_INF) continue;
-            busy = 1;
             const int sk = ((volatile int *)S.snk)[s];
             if (sk > 0) {
                 if (h > 0) {
@@ -233,81 +228,99 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
                 }
                 continue;
             }
-            // gather: residual and far-end label of every arc (slots as in gather_out),
-            // every load issued before any is used
+            // gather: residual and far-end label of every arc, every load issued before
+            // any is used
             int res[kMaxArcs], far_lab[kMaxArcs];
 #pragma unroll
-            for (int k = 0; k < kMaxArcs; ++k) {
-                int x2, y2, z2;
-                res[k] = 0;
-                far_lab[k] = POG_INF;
-                if (!far_node(g, soft, k, x, y, z, x2, y2, z2)) continue;
-                const Where w = where(x2, y2, z2);
-                const int d = k >= 2 ? (k - 2) / 3 : 0;
-                const int kind = k < 2 ? k : 2 + (k - 2) % 3;  // 0 down, 1 up, 2 hout, 3 hin, 4 soft
-                if (kind == 0) res[k] = POG_CAP_INF - ((volatile int *)S.fdn)[s];
-                else if (kind == 1) res[k] = w.in ? ((volatile int *)S.fdn)[w.s] : ldcg(g.fdn + w.gidx);
-                else if (kind == 2) res[k] = POG_CAP_INF - ((volatile int *)S.fh[d])[s];
-                else if (kind == 3) res[k] = w.in ? ((volatile int *)S.fh[d ^ 1])[w.s] : ldcg(g.fh[d ^ 1] + w.gidx);
-                else if (d & 1) res[k] = g.alpha - ((volatile int *)SS.gs[d >> 1])[s];
-                else res[k] = g.alpha + (w.in ? ((volatile int *)SS.gs[d >> 1])[w.s] : ldcg(g.gs[d >> 1] + w.gidx));
-                far_lab[k] = w.in ? vlab[w.s] : ldcg(g.lab + w.gidx);
+            for (int a = 0; a < kMaxArcs; ++a) {
+                res[a] = 0;
+                far_lab[a] = POG_INF;
+                const int d = a >= 2 ? (a - 2) / 3 : 0;
+                const int kind = a < 2 ? a : 2 + (a - 2) % 3;  // 0 down, 1 up, 2 hout, 3 hin, 4 soft
+                const int dx = a < 2 ? 0 : (d == 0 ? -1 : (d == 1 ? 1 : 0));
+                const int dy = a < 2 ? 0 : (d == 2 ? -1 : (d == 3 ? 1 : 0));
+                const int dz = kind == 0 ? -1 : (kind == 1 ? 1 : (kind == 2 ? -D : (kind == 3 ? D : 0)));
+                bool ok;
+                if (kind == 0) ok = z >= 2;
+                else if (kind == 1) ok = z + 1 < Z;
+                else {
+                    ok = (unsigned)(x + dx) < (unsigned)X && (unsigned)(y + dy) < (unsigned)Y;
+                    if (kind == 2) ok = ok && z - D >= 1;
+                    else if (kind == 3) ok = ok && z + D < Z;
+                    else ok = ok && soft;
+                }
+                if (!ok) continue;
+                const bool in = (unsigned)(cx + dx) < (unsigned)TX && (unsigned)(cy + dy) < (unsigned)TY &&
+                                (unsigned)(cz + dz) < (unsigned)TZ;
+                const int s2 = s + dz + (dy + dx * TY) * TZ;
+                const int u2 = u + dz + dy * Z + dx * sx;
+                if (kind == 0) res[a] = POG_CAP_INF - ((volatile int *)S.fdn)[s];
+                else if (kind == 1) res[a] = in ? ((volatile int *)S.fdn)[s2] : ldcg(g.fdn + u2);
+                else if (kind == 2) res[a] = POG_CAP_INF - ((volatile int *)S.fh[d])[s];
+                else if (kind == 3) res[a] = in ? ((volatile int *)S.fh[d ^ 1])[s2] : ldcg(g.fh[d ^ 1] + u2);
+                else if (d & 1) res[a] = g.alpha - ((volatile int *)SS.gs[d >> 1])[s];
+                else res[a] = g.alpha + (in ? ((volatile int *)SS.gs[d >> 1])[s2] : ldcg(g.gs[d >> 1] + u2));
+                far_lab[a] = in ? vlab[s2] : ldcg(g.lab + u2);
             }
             int best = POG_INF, bk = -1, bres = 0;
 #pragma unroll
-            for (int k = 0; k < kMaxArcs; ++k)
-                if (res[k] > 0 && far_lab[k] < best) {
-                    best = far_lab[k];
-                    bk = k;
-                    bres = res[k];
+            for (int a = 0; a < kMaxArcs; ++a)
+                if (res[a] > 0 && far_lab[a] < best) {
+                    best = far_lab[a];
+                    bk = a;
+                    bres = res[a];
                 }
             if (bk < 0 || h <= best) {  // relabel (Algorithm 2)
                 S.lab[s] = best >= POG_INF - 1 ? POG_INF : best + 1;
                 continue;
             }
-            int x2, y2, z2;
-            far_node(g, soft, bk, x, y, z, x2, y2, z2);
-            const Where bw = where(x2, y2, z2);
+            // push along arc bk (Algorithm 2)
             const int bd = bk >= 2 ? (bk - 2) / 3 : 0;
             const int bkind = bk < 2 ? bk : 2 + (bk - 2) % 3;
+            const int bdx = bk < 2 ? 0 : (bd == 0 ? -1 : (bd == 1 ? 1 : 0));
+            const int bdy = bk < 2 ? 0 : (bd == 2 ? -1 : (bd == 3 ? 1 : 0));
+            const int bdz = bkind == 0 ? -1 : (bkind == 1 ? 1 : (bkind == 2 ? -D : (bkind == 3 ? D : 0)));
+            const int tcx = cx + bdx, tcy = cy + bdy, tcz = cz + bdz;  // target, tile-local
+            const bool bin = (unsigned)tcx < (unsigned)TX && (unsigned)tcy < (unsigned)TY && (unsigned)tcz < (unsigned)TZ;
+            const int bs = s + bdz + (bdy + bdx * TY) * TZ;
+            const int bu = u + bdz + bdy * Z + bdx * sx;
             const int delta = e < bres ? e : bres;
             int sat = 0;
             switch (bkind) {
                 case 0: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
                 case 1:
-                    if (bw.in) atomicSub(&S.fdn[bw.s], delta);
-                    else atomicSub(g.fdn + bw.gidx, delta);
+                    if (bin) atomicSub(&S.fdn[bs], delta);
+                    else atomicSub(g.fdn + bu, delta);
                     break;
                 case 2: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
                 case 3:
-                    if (bw.in) atomicSub(&S.fh[bd ^ 1][bw.s], delta);
-                    else atomicSub(g.fh[bd ^ 1] + bw.gidx, delta);
+                    if (bin) atomicSub(&S.fh[bd ^ 1][bs], delta);
+                    else atomicSub(g.fh[bd ^ 1] + bu, delta);
                     break;
                 default:
                     if (bd & 1) atomicAdd(&SS.gs[bd >> 1][s], delta);
-                    else if (bw.in) atomicSub(&SS.gs[bd >> 1][bw.s], delta);
-                    else atomicSub(g.gs[bd >> 1] + bw.gidx, delta);
+                    else if (bin) atomicSub(&SS.gs[bd >> 1][bs], delta);
+                    else atomicSub(g.gs[bd >> 1] + bu, delta);
                     break;
             }
             atomicSub(&S.exc[s], delta);
             int old;
-            if (bw.in) old = atomicAdd(&S.exc[bw.s], delta);
-            else old = atomicAdd(g.exc + bw.gidx, delta);
+            if (bin) old = atomicAdd(&S.exc[bs], delta);
+            else old = atomicAdd(g.exc + bu, delta);
             if (old > 0x7fffffff - delta) sat = 1;
             if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
-            if (!bw.in) {  // the receiving tile has work next sweep
-                const int dz = z2 < z0 ? 0 : (z2 < z0 + TZ ? 1 : 2);
-                if (z2 >= z0 - TZ && z2 < z0 + 2 * TZ) {
-                    const int dx = x2 < x0 ? 0 : (x2 < x0 + TX ? 1 : 2);
-                    const int dy = y2 < y0 ? 0 : (y2 < y0 + TY ? 1 : 2);
-                    atomicOr(&S.nb, 1u << (dx * 9 + dy * 3 + dz));
+            if (!bin) {  // the receiving tile has work next sweep
+                if (tcz >= -TZ && tcz < 2 * TZ) {
+                    const int mx = tcx < 0 ? 0 : (tcx < TX ? 1 : 2);
+                    const int my = tcy < 0 ? 0 : (tcy < TY ? 1 : 2);
+                    const int mz = tcz < 0 ? 0 : (tcz < TZ ? 1 : 2);
+                    atomicOr(&S.nb, 1u << (mx * 9 + my * 3 + mz));
                 } else {  // a vertical offset longer than a tile
-                    list_tile(tile - local_tile + ((x2 / TX) * nty + (y2 / TY)) * ntz + z2 / TZ, L.nflag, L.nlist,
-                              L.ncount);
+                    list_tile(tile - local_tile + (((x0 + tcx) / TX) * nty + (y0 + tcy) / TY) * ntz + (z0 + tcz) / TZ,
+                              L.nflag, L.nlist, L.ncount);
                 }
             }
         }
-        if (!__any_sync(0xffffffffu, busy)) break;
     }
     __syncthreads();
     int still = 0;  // does the tile keep an active node for the next sweep?
