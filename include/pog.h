@@ -62,7 +62,8 @@ typedef struct {
     int32_t max_rounds;         /* cap on global-relabel rounds before POG_E_NOCONVERGE */
     int32_t tile_sweeps;        /* local push/relabel sweeps per shared-memory tile visit */
     int32_t flags;              /* POG_FLAG_* bits */
-    int32_t bfs_blocks_per_sm;  /* resident blocks per SM of the cooperative BFS launches */
+    int32_t bfs_blocks_per_sm;  /* blocks per SM of the cooperative BFS launches: 1, 2 or 4 (of 1024,
+                                   512 or 256 threads); 0 or other values: 4 */
     float relabel_factor;       /* adaptive mode: sweep time per round / global relabel time */
     int32_t tile_shape;         /* 0: 4x8 columns x 32 heights, 1: 8x8x16, 2: 4x4x64, 3: 2x4x128 */
     int32_t bfs_bottom_up_ratio; /* BFS level runs bottom-up when frontier * ratio > unlabelled

@@ -25,7 +25,7 @@ SPACE = {
     "tile_shape": [0, 1, 2, 3],
     "tile_sweeps": [4, 8, 16, 32],
     "relabel_factor": [0.5, 1.0, 2.0, 4.0],
-    "bfs_blocks_per_sm": [2, 4, 8],
+    "bfs_blocks_per_sm": [1, 2, 4],
     "bfs_bottom_up_ratio": [4, 8, 16, -1],
 }
 DEFAULTS = {"sweeps_per_relabel": 0, "tile_shape": 0, "tile_sweeps": 8, "relabel_factor": 1.0,
@@ -45,8 +45,23 @@ def load_table(path: str = TUNED_PATH) -> dict:
 
 
 def tuned_params(X, Y, Z, delta, alpha, path: str = TUNED_PATH) -> dict:
-    """Tuned parameters for this volume class, else the defaults."""
-    entry = load_table(path).get(volume_key(X, Y, Z, delta, alpha))
+    """Tuned parameters for this volume class; else those of the tuned class with the same
+    delta and alpha that is closest in node count; else the defaults."""
+    table = load_table(path)
+    entry = table.get(volume_key(X, Y, Z, delta, alpha))
+    if entry is None:
+        n = X * Y * Z
+        near = []
+        for key, e in table.items():
+            try:
+                shape, d, a = key.split("/")
+                dims = [int(v) for v in shape.split("x")]
+            except ValueError:
+                continue
+            if d == f"d{delta}" and a == f"a{alpha}" and len(dims) == 3:
+                near.append((abs(dims[0] * dims[1] * dims[2] - n), key))
+        if near:
+            entry = table[min(near)[1]]
     params = dict(DEFAULTS)
     if entry:
         params.update(entry["params"])

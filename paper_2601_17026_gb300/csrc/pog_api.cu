@@ -224,9 +224,9 @@ pog_status maxflow_impl(pog_graph *g) {
                     return pog::launch_sweep(g->live, g->queue_a, &g->bfs_sync->size[0], kNodeOps, g->stream);
                 const cudaError_t e = pog::launch_tile_sweep(
                     g->live, g->nlive == 1 ? &g->live_vols[0] : nullptr, g->live_tile_base[0], g->any_soft,
-                    g->tile_shape, g->tiles, g->ntiles, g->tile_work, g->tile_parity, k == 0, g->tile_sweeps,
+                    g->tile_shape, g->tiles, g->ntiles, g->tile_work, g->tile_serial, k == 0, g->tile_sweeps,
                     g->stream);
-                g->tile_parity ^= 1;
+                ++g->tile_serial;
                 return e;
             }));
             if (gap && k + 1 == half) {
@@ -239,7 +239,9 @@ pog_status maxflow_impl(pog_graph *g) {
         }
         POG_TRY_CUDA(cudaEventRecord(g->round_ev[3], g->stream));
         g->stats[ST_SWEEP] += sweeps;
-        g->stats[ST_LAUNCHES] += 2 * sweeps;
+        // node sweeps: collect + push per sweep; tiled: the tile kernel per sweep, and the
+        // list reset + activity scan on the first sweep of the round
+        g->stats[ST_LAUNCHES] += (g->flags & POG_FLAG_NODE_SWEEPS) ? 2 * sweeps : sweeps + 2;
         POG_TRY(global_relabel(g, active));
         g->stats[ST_ROUNDS]++;
         if (g->sweeps_per_relabel <= 0) {
@@ -386,7 +388,7 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->trace = reinterpret_cast<pog::LevelTrace *>(take(trace));
     g->tiles = reinterpret_cast<int32_t *>(take(4 * tile_bytes));
     g->ntiles = (long long)(tile_bytes / sizeof(int32_t));
-    g->tile_parity = 0;
+    g->tile_serial = 0;
     g->tile_work = reinterpret_cast<int32_t *>(take(256));
     g->vctr = reinterpret_cast<DevCounters *>(take(vctr));
     g->vols_dev = reinterpret_cast<Grid *>(take(align_up(sizeof(Grid) * n, 256)));
@@ -432,7 +434,7 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->vctr, 0, sizeof(DevCounters) * n, g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->tiles, 0, 4 * tile_bytes, g->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_work, 0, 4 * sizeof(int32_t), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->tile_work, 0, 6 * sizeof(int32_t), g->stream);
     for (int v = 0; v < n && e == cudaSuccess; ++v)
         e = timed(g, TM_BUILD, [&] { return launch(v, g->vols[v], g->stream); });
     if (e != cudaSuccess) {

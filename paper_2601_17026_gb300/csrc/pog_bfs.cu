@@ -21,32 +21,31 @@ namespace pog {
 
 namespace {
 
-constexpr int kBfsThreads = 256;
+// Each SM runs 1024 threads of a search grid, as 1, 2 or 4 blocks (fewer blocks: fewer
+// arrivals at every grid barrier).
+constexpr int kBfsSmThreads = 1024;
 constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1-2 s of polling at worst
 
-// Sense-reversing grid barrier over co-resident blocks; false once the wait timed out.
+// Grid barrier over co-resident blocks on one monotonic arrival counter (zeroed before
+// each launch): the k-th barrier is passed once the counter reaches k * nblocks. One
+// atomic per block and a polling load, no second word to flip. False once the wait
+// timed out (POG_ERR_TIMEOUT is raised and every block leaves).
 __device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err) {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned *gen = &s->gen;
-        const unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(&s->count, 1u) == nblocks - 1) {
-            s->count = 0;
-            __threadfence();
-            atomicAdd(&s->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > kBarrierSpinLimit || (*(volatile int *)err & POG_ERR_TIMEOUT)) {
-                    atomicOr(err, POG_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        __threadfence();  // this block's writes before its arrival
+        const unsigned old = atomicAdd(&s->count, 1u);
+        const unsigned target = (old / nblocks + 1) * nblocks;
+        long long spins = 0;
+        while ((int)(*(volatile unsigned *)&s->count - target) < 0) {
+            if (++spins > kBarrierSpinLimit || (*(volatile int *)err & POG_ERR_TIMEOUT)) {
+                atomicOr(err, POG_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            __nanosleep(20);
         }
         __threadfence();
     }
@@ -99,9 +98,40 @@ __device__ __forceinline__ void gather_in_any(const Grid &g, int v, int x, int y
 }
 
 template <bool RO>
-__device__ __forceinline__ void gather_out_any(const Grid &g, int u, int x, int y, int z, Hood &h) {
-    if (g.gs[0]) gather_out<true, RO>(g, u, x, y, z, h);
-    else gather_out<false, RO>(g, u, x, y, z, h);
+__device__ __forceinline__ void gather_out_any(const Grid &g, int u, int x, int y, int z, Hood &h,
+                                               const int32_t *far = nullptr) {
+    if (g.gs[0]) gather_out<true, RO>(g, u, x, y, z, h, far);
+    else gather_out<false, RO>(g, u, x, y, z, h, far);
+}
+
+// Bottom-up test of an unlabelled node u: does one of its residual out-arcs end at a
+// node of `level`? The far ends' labels are loaded first; residuals only for the arcs
+// whose far end is at `level` (most nodes have none).
+template <bool SOFT>
+__device__ __forceinline__ bool bottom_up_hit(const Grid &g, int u, int x, int y, int z, int level) {
+    int node[kMaxArcs];
+    unsigned at = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) {
+        int r;
+        if (out_arc<SOFT, true>(g, u, x, y, z, k, false, node[k], r)) at |= 1u << k;
+    }
+    int lab[kMaxArcs];
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) lab[k] = (at >> k & 1u) ? ldcg(g.lab + node[k]) : POG_INF;
+    unsigned cand = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) cand |= (lab[k] == level ? 1u : 0u) << k;
+    if (!cand) return false;
+    bool hit = false;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) {
+        if (!(cand >> k & 1u)) continue;
+        int nd, r;
+        out_arc<SOFT, true>(g, u, x, y, z, k, true, nd, r);
+        hit |= r > 0;
+    }
+    return hit;
 }
 
 // Union node bases of the batch in shared memory (kMaxVolumes + 1 ints).
@@ -110,8 +140,8 @@ __device__ __forceinline__ void load_bases(const Batch &b, int *sbase) {
     __syncthreads();
 }
 
-template <bool SINGLE>
-__global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, Grid g0, int *qa, int *qb,
+template <bool SINGLE, int THREADS>
+__global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_relabel(Batch b, Grid g0, int *qa, int *qb,
                                                                    BfsSync *sync, int bottom_up_ratio) {
     __shared__ int sbase[kMaxVolumes + 1];
     const unsigned nblocks = gridDim.x;
@@ -123,20 +153,46 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, Grid
     if (blockIdx.x == 0)  // per-volume termination counts, summed at the end
         for (int v = threadIdx.x; v < b.nvol; v += blockDim.x) b.vols[v].ctr->active = 0;
     long long unvisited = 0;
-    // level 1: nodes whose sink arc is residual; everything else starts unreachable
+    unsigned long long t_start = 0;
+    if (tid == 0 && b.trace) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    // levels 1 and 2 in one pass over the nodes: level 1 holds the nodes whose sink arc is
+    // residual, level 2 the others with a residual arc into level 1 (read off the far
+    // ends' sink residuals, which no step of the search changes); everything else starts
+    // unreachable. Only level 2 is queued.
+    int ones = 0;
     for (int v = 0; v < b.nvol; ++v) {
         const Grid g = SINGLE ? g0 : b.vols[v];
         const int base = sbase[v];
         unvisited += (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
         for (int u = tid; u < g.N; u += stride) {
-            const bool first = (u % g.Z != 0) && g.snk[u] > 0;
-            g.lab[u] = first ? 1 : POG_INF;
-            if (first) warp_append(base + u, qa, &s->size[1]);
+            int x, y, z;
+            decode(g, u, x, y, z);
+            int l = POG_INF;
+            if (z != 0) {
+                if (__ldg(g.snk + u) > 0) {
+                    l = 1;
+                } else {
+                    Hood hd;
+                    gather_out_any<true>(g, u, x, y, z, hd, g.snk);
+                    bool hit = false;
+#pragma unroll
+                    for (int k = 0; k < kMaxArcs; ++k) hit |= hd.res[k] > 0 && hd.lab[k] > 0;
+                    if (hit) l = 2;
+                }
+            }
+            g.lab[u] = l;
+            ones += l == 1;
+            if (l == 2) warp_append(base + u, qb, &s->size[2]);
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ones += __shfl_down_sync(0xffffffffu, ones, o);
+    if ((threadIdx.x & 31) == 0 && ones) atomicAdd(&s->level1, ones);
     if (!grid_sync(s, nblocks, err)) return;
-    int level = 1;
-    int *cur = qa, *nxt = qb;
+    unvisited -= *(volatile int *)&s->level1;
+    if (tid == 0 && b.trace) b.trace[0] = LevelTrace{*(volatile int *)&s->level1, 2, (long long)t_start, 0};
+    int level = 2;
+    int *cur = qb, *nxt = qa;
     __shared__ int frontier;
     for (;;) {
         if (threadIdx.x == 0) frontier = *(volatile int *)&s->size[level % 3];
@@ -165,11 +221,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, Grid
                     int x, y, z;
                     decode(g, u, x, y, z);
                     if (z == 0) continue;
-                    Hood hd;
-                    gather_out_any<true>(g, u, x, y, z, hd);
-                    bool hit = false;
-#pragma unroll
-                    for (int k = 0; k < kMaxArcs; ++k) hit |= hd.lab[k] == level;
+                    const bool hit = g.gs[0] ? bottom_up_hit<true>(g, u, x, y, z, level)
+                                             : bottom_up_hit<false>(g, u, x, y, z, level);
                     if (hit) {
                         g.lab[u] = level + 1;
                         warp_append(base + u, nxt, &s->size[(level + 1) % 3]);
@@ -235,8 +288,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_global_relabel(Batch b, Grid
     if (tid == 0) b.ctr->max_label = level;
 }
 
-template <bool SINGLE>
-__global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, Grid g0, int *qa, int *qb, BfsSync *sync) {
+template <bool SINGLE, int THREADS>
+__global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_cut_reach(Batch b, Grid g0, int *qa, int *qb, BfsSync *sync) {
     __shared__ int sbase[kMaxVolumes + 1];
     const unsigned nblocks = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,28 +351,34 @@ __global__ void __launch_bounds__(kBfsThreads, 4) k_cut_reach(Batch b, Grid g0, 
     if (tid == 0) b.ctr->max_label = level;
 }
 
-// Grid of a cooperative launch: `blocks_per_sm` (default 4) co-resident blocks per SM.
+// Grid of a cooperative launch of `threads`-thread blocks: as many per SM as make
+// 1024 threads, fewer if the occupancy calculator says they would not all be resident.
 template <class K>
-cudaError_t coop_blocks(K kernel, int blocks_per_sm, int &blocks) {
+cudaError_t coop_blocks(K kernel, int threads, int &blocks) {
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
     if (!coop) return cudaErrorNotSupported;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBfsThreads, 0)) != cudaSuccess) return e;
-    const int want = blocks_per_sm > 0 ? blocks_per_sm : 4;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0)) != cudaSuccess) return e;
+    const int want = kBfsSmThreads / threads;
     blocks = sms * (per_sm < want ? per_sm : want);  // co-resident by construction
     return blocks < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 
 template <class K>
-cudaError_t coop_launch(K kernel, void **args, BfsSync *sync, int blocks_per_sm, cudaStream_t st) {
+cudaError_t coop_launch(K kernel, int threads, void **args, BfsSync *sync, cudaStream_t st) {
     int blocks = 0;
-    cudaError_t e = coop_blocks(kernel, blocks_per_sm, blocks);
+    cudaError_t e = coop_blocks(kernel, threads, blocks);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sync, 0, sizeof(BfsSync), st)) != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(kernel), blocks, kBfsThreads, args, 0, st);
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(kernel), blocks, threads, args, 0, st);
+}
+
+// Blocks per SM (1, 2 or 4; 0 and other values: 4) to the block size.
+int bfs_threads(int blocks_per_sm) {
+    return blocks_per_sm == 1 ? 1024 : (blocks_per_sm == 2 ? 512 : 256);
 }
 
 }  // namespace
@@ -329,8 +388,15 @@ cudaError_t launch_global_relabel(const Batch &b, const Grid *single, int *qa, i
     Batch bb = b;
     Grid g0 = single ? *single : Grid{};
     void *args[] = {&bb, &g0, &qa, &qb, &sync, &bottom_up_ratio};
-    if (single) return coop_launch(k_global_relabel<true>, args, sync, blocks_per_sm, st);
-    return coop_launch(k_global_relabel<false>, args, sync, blocks_per_sm, st);
+    const int t = bfs_threads(blocks_per_sm);
+    if (single) {
+        if (t == 1024) return coop_launch(k_global_relabel<true, 1024>, t, args, sync, st);
+        if (t == 512) return coop_launch(k_global_relabel<true, 512>, t, args, sync, st);
+        return coop_launch(k_global_relabel<true, 256>, t, args, sync, st);
+    }
+    if (t == 1024) return coop_launch(k_global_relabel<false, 1024>, t, args, sync, st);
+    if (t == 512) return coop_launch(k_global_relabel<false, 512>, t, args, sync, st);
+    return coop_launch(k_global_relabel<false, 256>, t, args, sync, st);
 }
 
 cudaError_t launch_cut_reach(const Batch &b, const Grid *single, int *qa, int *qb, BfsSync *sync, int blocks_per_sm,
@@ -338,8 +404,15 @@ cudaError_t launch_cut_reach(const Batch &b, const Grid *single, int *qa, int *q
     Batch bb = b;
     Grid g0 = single ? *single : Grid{};
     void *args[] = {&bb, &g0, &qa, &qb, &sync};
-    if (single) return coop_launch(k_cut_reach<true>, args, sync, blocks_per_sm, st);
-    return coop_launch(k_cut_reach<false>, args, sync, blocks_per_sm, st);
+    const int t = bfs_threads(blocks_per_sm);
+    if (single) {
+        if (t == 1024) return coop_launch(k_cut_reach<true, 1024>, t, args, sync, st);
+        if (t == 512) return coop_launch(k_cut_reach<true, 512>, t, args, sync, st);
+        return coop_launch(k_cut_reach<true, 256>, t, args, sync, st);
+    }
+    if (t == 1024) return coop_launch(k_cut_reach<false, 1024>, t, args, sync, st);
+    if (t == 512) return coop_launch(k_cut_reach<false, 512>, t, args, sync, st);
+    return coop_launch(k_cut_reach<false, 256>, t, args, sync, st);
 }
 
 }  // namespace pog

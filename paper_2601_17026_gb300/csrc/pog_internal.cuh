@@ -50,14 +50,16 @@ struct DevCounters {
 
 // Grid-barrier and frontier-size words of a cooperative BFS launch.
 struct BfsSync {
-    unsigned count;  // blocks arrived at the current barrier
-    unsigned gen;    // barrier generation
+    unsigned count;  // barrier arrivals since the launch
+    unsigned gen;    // unused
     int size[3];     // frontier sizes, indexed by level mod 3
-    int pad[3];
+    int level1;      // nodes of level 1 (global relabel)
+    int pad[2];
 };
 
 // Per-level trace of the last global relabel: frontier size, mode (0 top-down, 1
-// bottom-up) and the device clock (ns) when the level started.
+// bottom-up, 2 the pass that labels levels 1 and 2) and the device clock (ns) when the
+// level started.
 constexpr int kTraceLevels = 4096;
 struct LevelTrace {
     long long size, mode, t_ns, pad;
@@ -137,8 +139,10 @@ __device__ __forceinline__ int ld_arc(const int32_t *p) {
 }
 
 // Out-arcs of u: slot 0 down, 1 up, 2+3d hard out, 3+3d hard in (reverse), 4+3d soft.
+// `far` (default: the labels) is the array read at each far end into h.lab.
 template <bool SOFT, bool RO = false>
-__device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, int z, Hood &h) {
+__device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, int z, Hood &h,
+                                           const int32_t *far = nullptr) {
 #pragma unroll
     for (int i = 0; i < kMaxArcs; ++i) {
         h.res[i] = 0;
@@ -172,11 +176,48 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
             h.res[4 + 3 * d] = (d & 1) ? g.alpha - ld_arc<RO>(g.gs[d >> 1] + u) : g.alpha + ld_arc<RO>(g.gs[d >> 1] + v);
         }
     }
+    const int32_t *fv = far ? far : g.lab;
 #pragma unroll
-    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = ldcg(g.lab + h.node[i]);  // one round trip with the residuals
+    for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = ldcg(fv + h.node[i]);  // one round trip with the residuals
 #pragma unroll
     for (int i = 0; i < kMaxArcs; ++i)
         if (h.res[i] <= 0) h.lab[i] = POG_INF;
+}
+
+// Out-arc slot k of u alone (slots as in gather_out): false when the arc is absent;
+// else its far end and, when `want_res`, its residual capacity.
+template <bool SOFT, bool RO = false>
+__device__ __forceinline__ bool out_arc(const Grid &g, int u, int x, int y, int z, int k, bool want_res, int &node,
+                                        int &res) {
+    res = 0;
+    if (k == 0) {
+        node = u - 1;
+        if (want_res && z >= 2) res = POG_CAP_INF - ld_arc<RO>(g.fdn + u);
+        return z >= 2;
+    }
+    if (k == 1) {
+        node = u + 1;
+        if (want_res && z + 1 < g.Z) res = ld_arc<RO>(g.fdn + u + 1);
+        return z + 1 < g.Z;
+    }
+    const int d = (k - 2) / 3, kind = (k - 2) % 3;
+    bool ok;
+    const int off = nb_offset(g, x, y, d, ok);
+    if (kind == 0) {
+        ok = ok && z - g.delta >= 1;
+        node = u + off - g.delta;
+        if (want_res && ok) res = POG_CAP_INF - ld_arc<RO>(g.fh[d] + u);
+    } else if (kind == 1) {
+        ok = ok && z + g.delta < g.Z;
+        node = u + off + g.delta;
+        if (want_res && ok) res = ld_arc<RO>(g.fh[d ^ 1] + node);
+    } else {
+        ok = ok && SOFT;
+        node = u + off;
+        if (want_res && ok)
+            res = (d & 1) ? g.alpha - ld_arc<RO>(g.gs[d >> 1] + u) : g.alpha + ld_arc<RO>(g.gs[d >> 1] + node);
+    }
+    return ok;
 }
 
 // In-arcs of v (arcs u -> v): slot 0 from above, 1 from below, 2+3d hard arc of
@@ -255,8 +296,8 @@ struct pog_graph {
     pog::LevelTrace *trace;      // device [kTraceLevels]: last global relabel
     int32_t *tiles;              // device [4][ntiles]: flag and list of two alternating sweep lists
     long long ntiles;
-    int32_t *tile_work;          // device [4]: per list, listed tiles and next tile to take
-    int tile_parity;             // list the next tiled sweep visits
+    int32_t *tile_work;          // device [6]: three (listed tiles, next tile to take) counter pairs
+    long long tile_serial;       // tiled sweeps run so far (selects lists and counters)
     pog::DevCounters *ctr;       // device: union counters
     pog::DevCounters *vctr;      // device [nvol]: per-volume counters
     pog::DevCounters *ctr_host;  // pinned host mirror of ctr followed by vctr

@@ -29,11 +29,12 @@ constexpr int kTileShapes = 4;
 long long tile_count(const Grid &g, int shape);
 long long tile_count_max(const Grid &g);
 // `tiles`: 4 arrays of `ntiles` ints (flag and list of two alternating sweep lists, all
-// flags zero at the start); `work`: 4 ints. `parity` alternates from sweep to sweep and
-// `full_scan` is set on the first sweep after each global relabel.
+// flags zero at the start); `work`: 6 ints, zero at the start. `serial` counts the
+// tiled sweeps run on these buffers; `full_scan` is set on the first sweep after each
+// global relabel.
 cudaError_t launch_tile_sweep(const Batch &b, const Grid *single, int single_tile_base, bool soft, int shape,
-                              int *tiles, long long ntiles, int *work, int parity, bool full_scan, int local_sweeps,
-                              cudaStream_t st);
+                              int *tiles, long long ntiles, int *work, long long serial, bool full_scan,
+                              int local_sweeps, cudaStream_t st);
 cudaError_t launch_surface_energy(const float *cost, float scale, const int32_t *h, int B, int X, int Y, int Z,
                                   int alpha, long long *out, cudaStream_t st);
 

@@ -162,7 +162,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     NA_TRY_CUDA(cudaMemsetAsync(uctr, 0, sizeof(pog::DevCounters), st));
     NA_TRY_CUDA(cudaMemsetAsync(g.ctr, 0, sizeof(pog::DevCounters), st));
     NA_TRY_CUDA(cudaMemsetAsync(tile_lists, 0, 4 * tiles * 4, st));
-    NA_TRY_CUDA(cudaMemsetAsync(tile_work, 0, 4 * sizeof(int32_t), st));
+    NA_TRY_CUDA(cudaMemsetAsync(tile_work, 0, 6 * sizeof(int32_t), st));
     NA_TRY_CUDA(pog::launch_build_i32(g, cost_dev, st));
 
     pog::DevCounters host[2];
@@ -170,7 +170,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     NA_TRY(read_counters(uctr, g.ctr, host, st));
     if (!(flags & POG_FLAG_NO_PREPUSH)) NA_TRY_CUDA(pog::launch_column_prepush(g, st));
     const bool soft = alpha > 0;
-    int parity = 0;
+    long long serial = 0;
     for (int round = 0;; ++round) {
         NA_TRY_CUDA(cudaMemsetAsync(&uctr->active, 0, sizeof(host[0].active), st));
         NA_TRY_CUDA(pog::launch_global_relabel(b, &g, queue_a, queue_b, sync, bfs_blocks, bu_ratio, st));
@@ -182,8 +182,8 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
                 NA_TRY_CUDA(pog::launch_sweep(b, queue_a, &sync->size[0], kNodeOps, st));
             else
                 NA_TRY_CUDA(pog::launch_tile_sweep(b, &g, 0, soft, shape, tile_lists, (long long)tiles, tile_work,
-                                                   parity, k == 0, tile_sweeps, st));
-            parity ^= 1;
+                                                   serial, k == 0, tile_sweeps, st));
+            ++serial;
             if (!(flags & POG_FLAG_NO_GAP) && k + 1 == sweeps / 2) {
                 NA_TRY_CUDA(cudaMemsetAsync(&uctr->max_label, 0, sizeof(int), st));
                 NA_TRY_CUDA(pog::launch_gap(b, gap_bits, kGapLevels, st));

@@ -105,6 +105,7 @@ struct TileLists {
     int *nlist;       // next sweep's tiles
     int *ncount;
     int *nflag;
+    int *zero;        // the counter pair of the sweep after next, zeroed here
 };
 
 // One visit of one tile: stage it in shared memory, run the local sweeps, write it back.
@@ -376,6 +377,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, 
     __shared__ int tile_id, local_tile;
     __shared__ Grid sg;
     const int ntiles = *L.count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // last read by the previous sweep
+        L.zero[0] = 0;
+        L.zero[1] = 0;
+    }
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -446,35 +451,35 @@ cudaError_t launch_tile_kernel(const Batch &b, const Grid *single, int single_ti
                 : launch_tile_instance<TX, TY, TZ, false, false>(b, g0, 0, L, local_sweeps, blocks, st);
 }
 
-// The tile lists of a sweep alternate between two buffers. Buffer p's tiles are visited;
-// visits list the next sweep's tiles in buffer 1-p (whose flags are all clear: every
-// visit clears its own flag in p). After a global relabel, activity is recomputed, and
-// volumes may have left the batch, so the first sweep of a round (`full_scan`) drops
-// buffer p's carried list and scans every node of the batch into it.
-// `tiles` holds [flag p][list p] for p = 0, 1 (4 arrays of `ntiles`); `work` holds
-// [count, next] per buffer. `soft`: some volume has alpha > 0; `single`: the view of the
-// only volume (whose tiles start at union tile `single_tile_base`), or null.
+// The tile lists of sweep k alternate between two buffers, k mod 2: buffer k's tiles are
+// visited, and visits list the next sweep's tiles in the other buffer (whose flags are
+// all clear: every visit clears its own flag). Their counters rotate through three
+// pairs, k mod 3: sweep k reads pair k, appends through pair k+1, and zeroes pair k+2
+// (last read by sweep k-1), so a sweep is one launch. After a global relabel, activity
+// is recomputed and volumes may have left the batch, so the first sweep of a round
+// (`full_scan`) drops its carried list and scans every node of the batch into it.
+// `tiles` holds [flag p][list p] for p = 0, 1 (4 arrays of `ntiles`); `work` 3 pairs
+// of ints, all zero before sweep 0. `soft`: some volume has alpha > 0; `single`: the view
+// of the only volume (whose tiles start at union tile `single_tile_base`), or null.
 cudaError_t launch_tile_sweep(const Batch &b, const Grid *single, int single_tile_base, bool soft, int shape,
-                              int *tiles, long long ntiles, int *work, int parity, bool full_scan, int local_sweeps,
-                              cudaStream_t st) {
+                              int *tiles, long long ntiles, int *work, long long serial, bool full_scan,
+                              int local_sweeps, cudaStream_t st) {
     if (shape < 0 || shape >= kTileShapes) shape = 0;
-    const int p = parity & 1, q = p ^ 1;
+    const int p = (int)(serial & 1), q = p ^ 1;
     int *flag[2] = {tiles, tiles + 2 * ntiles};
     int *list[2] = {tiles + ntiles, tiles + 3 * ntiles};
-    int *cnt[2] = {work, work + 2};
+    int *cnt = work + 2 * (int)(serial % 3);
+    int *ncnt = work + 2 * (int)((serial + 1) % 3);
+    int *zcnt = work + 2 * (int)((serial + 2) % 3);
     const int sms = sm_count();
     const int *sh = kShapes[shape];
-    cudaError_t e = cudaSuccess;
     if (full_scan) {
-        k_clear_listed<<<sms, 256, 0, st>>>(flag[p], list[p], cnt[p]);
-        e = cudaMemsetAsync(cnt[p], 0, sizeof(int), st);
-        if (e == cudaSuccess)
-            k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag[p], list[p], cnt[p]);
+        k_clear_listed<<<sms, 256, 0, st>>>(flag[p], list[p], cnt);
+        const cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag[p], list[p], cnt);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt[q], 0, 2 * sizeof(int), st);  // next list starts empty
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt[p] + 1, 0, sizeof(int), st);  // take from slot 0
-    if (e != cudaSuccess) return e;
-    TileLists L{list[p], cnt[p], flag[p], cnt[p] + 1, list[q], cnt[q], flag[q]};
+    TileLists L{list[p], cnt, flag[p], cnt + 1, list[q], ncnt, flag[q], zcnt};
     const int blocks = sms * 3;
     switch (shape) {
         case 1: return launch_tile_kernel<8, 8, 16>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);

@@ -216,6 +216,14 @@ def seismic_volume(seed: int = BASE_SEED) -> Volume:
     return Volume(horizon_cost(spec_seismic(seed)), delta=3, alpha=50, name="512x512x384 d3 a50")
 
 
+def seismic_crop(n: int = 256, seed: int = BASE_SEED) -> Volume:
+    """The n x n x 384 corner (x, y < n) of the 512 x 512 x 384 volume, same delta and alpha:
+    a smaller case of the same kernels, for profiling."""
+    v = seismic_volume(seed)
+    return Volume(np.ascontiguousarray(v.cost[:n, :n]), delta=v.delta, alpha=v.alpha,
+                  name=f"{n}x{n}x384 crop of 512x512x384 d3 a50")
+
+
 def batch_shapes(seed: int = BASE_SEED, count: int = 64):
     """(X, Y, Z, delta, alpha) of the uneven batch: X,Y ~ U{32..256}, Z ~ U{64..256},
     delta ~ {1,2,4}, alpha = 0 for even and 25 for odd volume indices."""
