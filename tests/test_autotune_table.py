@@ -1,0 +1,25 @@
+"""Host logic of the tuned-parameter table (no GPU)."""
+import json
+
+from paper_2601_17026_gb300 import autotune
+
+
+def test_exact_nearest_and_default(tmp_path):
+    path = tmp_path / "tuned.json"
+    table = {
+        "512x512x384/d3/a50": {"params": {"tile_shape": 1, "tile_sweeps": 16}},
+        "64x64x64/d3/a50": {"params": {"tile_shape": 2}},
+        "256x256x256/d2/a0": {"params": {"tile_shape": 3}},
+        "garbage": {"params": {"tile_shape": 0}},
+    }
+    path.write_text(json.dumps(table))
+    exact = autotune.tuned_params(512, 512, 384, 3, 50, path=str(path))
+    assert exact["tile_shape"] == 1 and exact["tile_sweeps"] == 16
+    assert exact["bfs_blocks_per_sm"] == autotune.DEFAULTS["bfs_blocks_per_sm"]
+    # closest node count among the same (delta, alpha): 256x256x384 is nearer 512^2x384 than 64^3
+    assert autotune.tuned_params(256, 256, 384, 3, 50, path=str(path))["tile_shape"] == 1
+    assert autotune.tuned_params(48, 48, 64, 3, 50, path=str(path))["tile_shape"] == 2
+    # no class with this delta and alpha: defaults
+    assert autotune.tuned_params(256, 256, 384, 2, 50, path=str(path)) == autotune.DEFAULTS
+    # missing table: defaults
+    assert autotune.tuned_params(8, 8, 8, 1, 0, path=str(tmp_path / "none.json")) == autotune.DEFAULTS
