@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import time
 
@@ -46,7 +47,7 @@ def load_table(path: str = TUNED_PATH) -> dict:
 
 def tuned_params(X, Y, Z, delta, alpha, path: str = TUNED_PATH) -> dict:
     """Tuned parameters for this volume class; else those of the tuned class with the same
-    delta and alpha that is closest in node count; else the defaults."""
+    delta and alpha whose node count is closest in ratio; else the defaults."""
     table = load_table(path)
     entry = table.get(volume_key(X, Y, Z, delta, alpha))
     if entry is None:
@@ -59,7 +60,7 @@ def tuned_params(X, Y, Z, delta, alpha, path: str = TUNED_PATH) -> dict:
             except ValueError:
                 continue
             if d == f"d{delta}" and a == f"a{alpha}" and len(dims) == 3:
-                near.append((abs(dims[0] * dims[1] * dims[2] - n), key))
+                near.append((abs(math.log(dims[0] * dims[1] * dims[2] / n)), key))
         if near:
             entry = table[min(near)[1]]
     params = dict(DEFAULTS)

@@ -16,7 +16,7 @@ def test_exact_nearest_and_default(tmp_path):
     exact = autotune.tuned_params(512, 512, 384, 3, 50, path=str(path))
     assert exact["tile_shape"] == 1 and exact["tile_sweeps"] == 16
     assert exact["bfs_blocks_per_sm"] == autotune.DEFAULTS["bfs_blocks_per_sm"]
-    # closest node count among the same (delta, alpha): 256x256x384 is nearer 512^2x384 than 64^3
+    # closest node count (in ratio) among the same (delta, alpha)
     assert autotune.tuned_params(256, 256, 384, 3, 50, path=str(path))["tile_shape"] == 1
     assert autotune.tuned_params(48, 48, 64, 3, 50, path=str(path))["tile_shape"] == 2
     # no class with this delta and alpha: defaults
