@@ -1,5 +1,6 @@
-"""Full-size cases. The 256^3 volume is compared with the oracle's stored result
-(tests/golden/medium.json, written by make_golden.py with the oracle alone). The
+"""Full-size cases. The 256^3 volume and the 64 uneven volumes of the batched workload
+are compared with the oracle's stored results (tests/golden/medium.json and batch.json,
+written by make_golden.py with the oracle alone). The
 512x512x384 workload, too large for the oracle to solve in a test, is solved in the
 launch configuration the benchmark times (the tuned options) and checked by properties
 that hold at any size, with the oracle's linear-time routines: the exported final state
@@ -56,3 +57,19 @@ def test_seismic_full_size_certificate():
     e, feasible = oracle.energy(vol.cost, h, vol.delta, vol.alpha)
     assert feasible
     assert flow == e + pins.identity_offset(vol.cost)  # max-flow = E*(h) + K for the construction
+
+
+def test_uneven_batch_matches_stored_oracle():
+    """The 64 uneven volumes (227M nodes) in one batched solve, against the oracle's
+    stored flow and surface of every volume (tests/golden/batch.json)."""
+    with open(os.path.join(GOLDEN, "batch.json")) as f:
+        ref = json.load(f)["volumes"]
+    vols = synth.batch_volumes()
+    assert len(vols) == len(ref)
+    costs = [torch.from_numpy(v.cost).cuda() for v in vols]
+    flows, heights = pog.pog_solve_batch(costs, [v.delta for v in vols], [v.alpha for v in vols])
+    for v, r, fl, h in zip(vols, ref, flows, heights):
+        assert list(v.cost.shape) == r["shape"] and (v.delta, v.alpha) == (r["delta"], r["alpha"])
+        assert fl == r["flow"], v.name
+        h = np.ascontiguousarray(h.cpu().numpy(), dtype=np.int32)
+        assert hashlib.sha256(h.tobytes()).hexdigest() == r["heights_sha256"], v.name
