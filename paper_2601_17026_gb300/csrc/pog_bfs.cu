@@ -276,8 +276,12 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
     for (int vi = 0; vi < b.nvol; ++vi) {
         const Grid g = SINGLE ? g0 : b.vols[vi];
         unsigned long long active = 0;
-        for (int u = tid; u < g.N; u += stride)
-            if (u % g.Z != 0 && g.exc[u] > 0 && g.lab[u] < POG_INF) ++active;
+        for (int u = tid; u < g.N; u += stride) {
+            if (u % g.Z == 0) continue;
+            const int e = g.exc[u];
+            if (e < 0) atomicOr(err, POG_ERR_FLOW_RANGE);  // a wrapped excess
+            if (e > 0 && g.lab[u] < POG_INF) ++active;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(0xffffffffu, active, o);
         if ((threadIdx.x & 31) == 0 && active) {

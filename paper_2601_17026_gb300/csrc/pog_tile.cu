@@ -137,6 +137,7 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
         const int u = node[k];
         S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
         const int e = own[k] ? ldcg(g.exc + u) : 0;
+        if (e < 0) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes from outside
         S.exc[s] = e;
         S.exc0[s] = e;
         S.snk[s] = own[k] ? ldcg(g.snk + u) : 0;
@@ -305,10 +306,19 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
                     break;
             }
             atomicSub(&S.exc[s], delta);
-            int old;
-            if (bin) old = atomicAdd(&S.exc[bs], delta);
-            else old = atomicAdd(g.exc + bu, delta);
-            if (old > 0x7fffffff - delta) sat = 1;
+            // Overflow of the receiver's excess: checked here for pushes inside the tile
+            // and for large pushes out of it. A small push out of it (below 2^20) is
+            // fire-and-forget: a tile visit brings in fewer than 2^28 of them per node,
+            // so a wrap leaves the excess negative until the receiver's next load (its
+            // tile is listed for the next sweep) or the next global relabel, which both
+            // flag negative excess.
+            if (bin) {
+                if (atomicAdd(&S.exc[bs], delta) > 0x7fffffff - delta) sat = 1;
+            } else if (delta >= (1 << 20)) {
+                if (atomicAdd(g.exc + bu, delta) > 0x7fffffff - delta) sat = 1;
+            } else {
+                atomicAdd(g.exc + bu, delta);
+            }
             if (sat) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
             if (!bin) {  // the receiving tile has work next sweep
                 if (tcz >= -TZ && tcz < 2 * TZ) {
