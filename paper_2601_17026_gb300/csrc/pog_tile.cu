@@ -1,16 +1,15 @@
 // Tiled push/relabel (Section 3.2.1's column segments, mapped to thread blocks): a block
 // stages one tile of TX x TY columns x TZ heights of residual state in shared memory,
 // runs several local push/relabel sweeps on it (Algorithm 2, lock-free in the manner of
-// the node kernels), and writes the tile back. Only tiles holding an active node are
-// visited.
+// the node kernels), and stores its labels and sink residuals back. Only tiles holding an
+// active node are visited.
 //
 // Ownership rules that keep concurrent tiles consistent:
 //   * a node's label and sink residual change only in the tile that owns the node;
-//   * every arc value is stored at one node, hence staged by one tile; a neighbouring
-//     tile pushing along such an arc (or its reverse) uses a global atomic on the stored
-//     copy, and the owning tile writes its own change back as an atomic delta;
-//   * excess is likewise written back as a delta, so pushes that arrive from outside
-//     during the pass are kept.
+//   * every other word (excess, arc flows) may also be changed by neighbouring tiles, so
+//     each push applies its changes both to the shared image (for this tile's later
+//     reads) and to the global copy (by atomics that return nothing), exactly as a node
+//     kernel would; nothing of these words is written back.
 // Each tile only ever reads values that other tiles can move in the direction that
 // shrinks its own pushes, as in the node kernels, so the preflow stays valid.
 #include "pog_internal.cuh"
@@ -23,6 +22,7 @@ namespace {
 constexpr int kTileNodes = 1024;  // nodes per tile, every shape
 constexpr int kTileThreads = 256;
 constexpr int kPerThread = kTileNodes / kTileThreads;  // 4
+constexpr int kTileBlocksPerSm = 4;                 // resident tile visits per SM
 
 // Tile shapes (columns in x, columns in y, heights), all of 1024 nodes. Node s of a tile
 // sits at column c = s / TZ, height z0 + s % TZ, so consecutive threads read
@@ -81,18 +81,17 @@ __global__ void __launch_bounds__(256) k_clear_listed(int *flag, const int *list
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flag[list[i]] = 0;
 }
 
-// Shared-memory image of a tile: current values and the values at load time (for the
-// delta write-back). Arrays are indexed by the node's place s in the tile.
+// Shared-memory image of a tile, indexed by the node's place s in the tile. Every change
+// a visit makes to a word that other tiles may also change (excess and arc words) is
+// applied to the global copy at once as well (fire-and-forget atomics), so the image
+// only serves reads; the owner-only words (label, sink residual) are stored at the end.
 struct TileSmem {
     int lab[kTileNodes], exc[kTileNodes], snk[kTileNodes], fdn[kTileNodes];
     int fh[4][kTileNodes];
-    int exc0[kTileNodes], fdn0[kTileNodes];
-    int fh0[4][kTileNodes];
     unsigned nb;  // neighbour tiles pushed into: bit (dx+1)*9 + (dy+1)*3 + (dz+1)
 };
 struct TileSoft {
     int gs[2][kTileNodes];
-    int gs0[2][kTileNodes];
 };
 
 // Lists of a tiled sweep: the tiles to visit now, and the next sweep's tiles (those a
@@ -137,26 +136,15 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
         const int u = node[k];
         S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
         const int e = own[k] ? ldcg(g.exc + u) : 0;
-        if (e < 0) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes from outside
+        if (e < 0) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes
         S.exc[s] = e;
-        S.exc0[s] = e;
         S.snk[s] = own[k] ? ldcg(g.snk + u) : 0;
-        const int f = own[k] ? ldcg(g.fdn + u) : 0;
-        S.fdn[s] = f;
-        S.fdn0[s] = f;
+        S.fdn[s] = own[k] ? ldcg(g.fdn + u) : 0;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const int v = own[k] ? ldcg(g.fh[d] + u) : 0;
-            S.fh[d][s] = v;
-            S.fh0[d][s] = v;
-        }
+        for (int d = 0; d < 4; ++d) S.fh[d][s] = own[k] ? ldcg(g.fh[d] + u) : 0;
         if (soft) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int v = own[k] ? ldcg(g.gs[j] + u) : 0;
-                SS.gs[j][s] = v;
-                SS.gs0[j][s] = v;
-            }
+            for (int j = 0; j < 2; ++j) SS.gs[j][s] = own[k] ? ldcg(g.gs[j] + u) : 0;
         }
     }
     __syncthreads();
@@ -225,6 +213,7 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
                     const int d = e < sk ? e : sk;
                     S.snk[s] = sk - d;
                     atomicSub(&S.exc[s], d);
+                    atomicSub(g.exc + u, d);
                 } else {
                     S.lab[s] = 1;
                 }
@@ -289,32 +278,41 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
             const int delta = e < bres ? e : bres;
             int sat = 0;
             switch (bkind) {
-                case 0: sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF; break;
+                case 0:
+                    sat = atomicAdd(&S.fdn[s], delta) + delta == POG_CAP_INF;
+                    atomicAdd(g.fdn + u, delta);
+                    break;
                 case 1:
                     if (bin) atomicSub(&S.fdn[bs], delta);
-                    else atomicSub(g.fdn + bu, delta);
+                    atomicSub(g.fdn + bu, delta);
                     break;
-                case 2: sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF; break;
+                case 2:
+                    sat = atomicAdd(&S.fh[bd][s], delta) + delta == POG_CAP_INF;
+                    atomicAdd(g.fh[bd] + u, delta);
+                    break;
                 case 3:
                     if (bin) atomicSub(&S.fh[bd ^ 1][bs], delta);
-                    else atomicSub(g.fh[bd ^ 1] + bu, delta);
+                    atomicSub(g.fh[bd ^ 1] + bu, delta);
                     break;
                 default:
-                    if (bd & 1) atomicAdd(&SS.gs[bd >> 1][s], delta);
-                    else if (bin) atomicSub(&SS.gs[bd >> 1][bs], delta);
-                    else atomicSub(g.gs[bd >> 1] + bu, delta);
+                    if (bd & 1) {
+                        atomicAdd(&SS.gs[bd >> 1][s], delta);
+                        atomicAdd(g.gs[bd >> 1] + u, delta);
+                    } else {
+                        if (bin) atomicSub(&SS.gs[bd >> 1][bs], delta);
+                        atomicSub(g.gs[bd >> 1] + bu, delta);
+                    }
                     break;
             }
             atomicSub(&S.exc[s], delta);
-            // Overflow of the receiver's excess: checked here for pushes inside the tile
-            // and for large pushes out of it. A small push out of it (below 2^20) is
-            // fire-and-forget: a tile visit brings in fewer than 2^28 of them per node,
-            // so a wrap leaves the excess negative until the receiver's next load (its
-            // tile is listed for the next sweep) or the next global relabel, which both
-            // flag negative excess.
-            if (bin) {
-                if (atomicAdd(&S.exc[bs], delta) > 0x7fffffff - delta) sat = 1;
-            } else if (delta >= (1 << 20)) {
+            atomicSub(g.exc + u, delta);
+            if (bin) atomicAdd(&S.exc[bs], delta);
+            // Overflow of the receiver's excess, on the global copy: checked here for large
+            // pushes. A small push (below 2^20) is fire-and-forget: a tile visit brings in
+            // fewer than 2^28 of them per node, so a wrap leaves the excess negative until
+            // the receiver's next load (its tile is listed for the next sweep) or the next
+            // global relabel, which both flag negative excess.
+            if (delta >= (1 << 20)) {
                 if (atomicAdd(g.exc + bu, delta) > 0x7fffffff - delta) sat = 1;
             } else {
                 atomicAdd(g.exc + bu, delta);
@@ -348,30 +346,13 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
     }
     if (threadIdx.x == 0) atomicAdd(&b.ctr->tiles_visited, 1ull);
 
-    // ---- write back: owner-only words by store, shared words as deltas
+    // ---- write back the owner-only words
 #pragma unroll
     for (int k = 0; k < kPerThread; ++k) {
         if (!own[k]) continue;
         const int s = threadIdx.x + kTileThreads * k;
-        const int u = node[k];
-        g.lab[u] = S.lab[s];
-        g.snk[u] = S.snk[s];
-        int d = S.exc[s] - S.exc0[s];
-        if (d) atomicAdd(g.exc + u, d);
-        d = S.fdn[s] - S.fdn0[s];
-        if (d) atomicAdd(g.fdn + u, d);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            d = S.fh[j][s] - S.fh0[j][s];
-            if (d) atomicAdd(g.fh[j] + u, d);
-        }
-        if (soft) {
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                d = SS.gs[j][s] - SS.gs0[j][s];
-                if (d) atomicAdd(g.gs[j] + u, d);
-            }
-        }
+        g.lab[node[k]] = S.lab[s];
+        g.snk[node[k]] = S.snk[s];
     }
 }
 
@@ -379,7 +360,7 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
 // whether a given tile uses them is decided per volume. SINGLE: a batch of one volume,
 // whose view comes in as a kernel parameter (read from the constant bank).
 template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
-__global__ void __launch_bounds__(kTileThreads, 3) k_tile_push_relabel(Batch b, Grid g0, int tile_base0, TileLists L,
+__global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSm) k_tile_push_relabel(Batch b, Grid g0, int tile_base0, TileLists L,
                                                                     int local_sweeps) {
     extern __shared__ int4 smem_raw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
@@ -490,7 +471,7 @@ cudaError_t launch_tile_sweep(const Batch &b, const Grid *single, int single_til
         k_collect_tiles<<<sms * 8, 256, 0, st>>>(b, sh[0], sh[1], sh[2], flag[p], list[p], cnt);
     }
     TileLists L{list[p], cnt, flag[p], cnt + 1, list[q], ncnt, flag[q], zcnt};
-    const int blocks = sms * 3;
+    const int blocks = sms * kTileBlocksPerSm;
     switch (shape) {
         case 1: return launch_tile_kernel<8, 8, 16>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);
         case 2: return launch_tile_kernel<4, 4, 64>(b, single, single_tile_base, soft, L, local_sweeps, blocks, st);
