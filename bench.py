@@ -108,6 +108,25 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of this rank's values over all ranks of the initialised
+    process group (the values themselves without one, or at one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(ranks, nodes, steps, ms):
+    """Whole-job Mnodes/s of independent replicas: every rank's nodes over the slowest
+    rank's time."""
+    return ranks * nodes * steps / (ms / 1e3) / 1e6
+
+
 def algorithmic_bytes(N, alpha, tiles_per_sweep, scans_per_sweep):
     """Per-launch algorithmic bytes of each kernel family.
 
@@ -209,19 +228,14 @@ def run_ours(args):
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
-    times = [ms, e2e_ms]
-    if ws > 1:
-        t = torch.tensor(times, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        times = t.tolist()
-    ms, e2e_ms = times
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], device="cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
 
     per_step = ms / args.steps
-    value = ws * N * args.steps / (ms / 1e3) / 1e6
-    e2e_value = ws * N * args.steps / (e2e_ms / 1e3) / 1e6
+    value = job_throughput(ws, N, args.steps, ms)
+    e2e_value = job_throughput(ws, N, args.steps, e2e_ms)
     # roofline of the dominant kernel family, timed live with events on the solve stream
     tiles_per_sweep = sum(s["tiles_visited"] for s in stats) / max(sum(s["sweeps"] for s in stats), 1)
     scans_per_sweep = sum(s["rounds"] - 1 for s in stats) / max(sum(s["sweeps"] for s in stats), 1)
