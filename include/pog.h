@@ -107,8 +107,9 @@ typedef struct pog_graph pog_graph; /* opaque; owns its device state */
  *   opt      : host, may be NULL (defaults).
  *   stream   : cudaStream_t for all device work of this graph.
  *   out      : host, receives the new graph; unchanged on error.
- * Allocates device state of about 40 bytes per node (32 when alpha == 0). Work is
- * enqueued on `stream`; `cost_dev` must stay valid until that work has run.
+ * Allocates about 48 bytes per node on the device (40 when alpha == 0): the residual
+ * state and two search queues, plus a few small tables. Work is enqueued on `stream`;
+ * `cost_dev` must stay valid until that work has run.
  */
 POG_API pog_status pog_build(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta,
                      int32_t alpha, const pog_options *opt, void *stream, pog_graph **out);
