@@ -291,21 +291,26 @@ def batched_leg(args, warmup=1, steps=1):
 
     from paper_2601_17026_gb300 import pog, synth
 
+    from paper_2601_17026_gb300 import autotune
+
     vols = synth.batch_volumes()
     costs = [torch.from_numpy(v.cost).cuda() for v in vols]
     deltas = [v.delta for v in vols]
     alphas = [v.alpha for v in vols]
+    params = autotune.batch_params("uneven-64")
+    opts = pog.make_options(**params)
     for _ in range(warmup):
-        pog.pog_solve_batch(costs, deltas, alphas)
+        pog.pog_solve_batch(costs, deltas, alphas, opts)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(steps):
-        flows, heights = pog.pog_solve_batch(costs, deltas, alphas)
+        flows, heights = pog.pog_solve_batch(costs, deltas, alphas, opts)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t) / steps
     n = sum(v.n for v in vols)
     out = {"value": round(n / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2), "volumes": len(vols),
-           "nodes": n, "driver": "one solve of the disjoint union of the volumes; finished volumes leave at each global relabel"}
+           "nodes": n, "driver": "one solve of the disjoint union of the volumes; finished volumes leave at each global relabel",
+           "params": params}
     gold = os.path.join(ROOT, "tests", "golden", "batch.json")
     if os.path.exists(gold):
         with open(gold) as f:

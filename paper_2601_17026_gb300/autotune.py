@@ -69,6 +69,15 @@ def tuned_params(X, Y, Z, delta, alpha, path: str = TUNED_PATH) -> dict:
     return params
 
 
+def batch_params(name: str = "uneven-64", path: str = TUNED_PATH) -> dict:
+    """Parameters recorded for a batched workload (key ``batch/<name>``), else the defaults."""
+    params = dict(DEFAULTS)
+    entry = load_table(path).get(f"batch/{name}")
+    if entry:
+        params.update(entry["params"])
+    return params
+
+
 def options_for(X, Y, Z, delta, alpha, flags: int = 0, path: str = TUNED_PATH):
     from . import pog
 

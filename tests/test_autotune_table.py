@@ -23,3 +23,14 @@ def test_exact_nearest_and_default(tmp_path):
     assert autotune.tuned_params(256, 256, 384, 2, 50, path=str(path)) == autotune.DEFAULTS
     # missing table: defaults
     assert autotune.tuned_params(8, 8, 8, 1, 0, path=str(tmp_path / "none.json")) == autotune.DEFAULTS
+
+
+def test_batch_params(tmp_path):
+    path = tmp_path / "tuned.json"
+    path.write_text(json.dumps({"batch/uneven-64": {"params": {"tile_sweeps": 16}},
+                                "512x512x384/d3/a50": {"params": {"tile_shape": 1}}}))
+    got = autotune.batch_params("uneven-64", path=str(path))
+    assert got["tile_sweeps"] == 16 and got["tile_shape"] == autotune.DEFAULTS["tile_shape"]
+    assert autotune.batch_params("other", path=str(path)) == autotune.DEFAULTS
+    # the batch entry is not a volume class: the nearest-class lookup skips it
+    assert autotune.tuned_params(256, 256, 384, 3, 50, path=str(path))["tile_shape"] == 1
