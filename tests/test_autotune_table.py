@@ -34,3 +34,30 @@ def test_batch_params(tmp_path):
     assert autotune.batch_params("other", path=str(path)) == autotune.DEFAULTS
     # the batch entry is not a volume class: the nearest-class lookup skips it
     assert autotune.tuned_params(256, 256, 384, 3, 50, path=str(path))["tile_shape"] == 1
+
+
+def test_coordinate_descent_keeps_the_fastest(monkeypatch):
+    """tune() walks SPACE one parameter at a time from DEFAULTS and keeps a change only when
+    it is faster; a candidate that changes the flow value is an error."""
+    cost_of = {"tile_sweeps": {16: -0.3, 32: -0.1}, "tile_shape": {1: -0.2}, "bfs_blocks_per_sm": {2: +0.5}}
+
+    def fake_time(cost, delta, alpha, params, repeats):
+        t = 1.0
+        for name, table in cost_of.items():
+            t += table.get(params[name], 0.0)
+        return t, 12345
+
+    monkeypatch.setattr(autotune, "_time_solve", fake_time)
+    out = autotune.tune(None, 3, 50, log=lambda *_: None)
+    assert out["params"]["tile_sweeps"] == 16 and out["params"]["tile_shape"] == 1
+    assert out["params"]["bfs_blocks_per_sm"] == autotune.DEFAULTS["bfs_blocks_per_sm"]
+    assert abs(out["seconds"] - 0.5) < 1e-9
+
+    def wrong_flow(cost, delta, alpha, params, repeats):
+        return 1.0, 1 if params == autotune.DEFAULTS else 2
+
+    monkeypatch.setattr(autotune, "_time_solve", wrong_flow)
+    import pytest
+
+    with pytest.raises(RuntimeError):
+        autotune.tune(None, 3, 50, log=lambda *_: None)
