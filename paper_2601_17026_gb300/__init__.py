@@ -3,6 +3,7 @@
 ``pog``        thin binding of the C ABI (libpog.so, include/pog.h)
 ``autograd``   differentiable solve (quantise -> solve -> exact subgradient backward)
 ``synth``      seeded synthetic layered-horizon cost volumes
+``autotune``   per-volume-class launch options (coordinate descent over timed solves), ``tuned.json``
 ``build``      nvcc build of libpog.so for sm_103a
 """
 from .pog import (PogError, make_options, pog_backward, pog_build, pog_build_f32,  # noqa: F401
