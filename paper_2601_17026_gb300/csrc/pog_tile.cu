@@ -10,8 +10,10 @@
 //     each push applies its changes both to the shared image (for this tile's later
 //     reads) and to the global copy (by atomics that return nothing), exactly as a node
 //     kernel would; nothing of these words is written back.
-// Each tile only ever reads values that other tiles can move in the direction that
-// shrinks its own pushes, as in the node kernels, so the preflow stays valid.
+// Every residual capacity and excess a tile reads can only grow through other tiles'
+// concurrent pushes (they add flow in the reverse direction, or excess), so a stale read
+// never lets a tile push more than is there and the preflow stays valid, as in the node
+// kernels; a stale label of a neighbour (too low) can cost convergence, never validity.
 #include "pog_internal.cuh"
 #include "pog_launch.h"
 
