@@ -1,8 +1,9 @@
 """The oracle pinned to answers that do not come from itself (CPU only).
 
 Pins: brute-force enumeration, the single-row dynamic program, the delta >= Z-1
-closed form, the flow/energy identity, and the invariants of Section 1.3 (Eq. 2-4
-and Theorem 1.1) checked inside the C code. ``test_planted_mistakes`` compiles the
+closed form, the flow/energy identity, the invariants of Section 1.3 (Eq. 2-4
+and Theorem 1.1) checked inside the C code, and a library max-flow (scipy's
+Edmonds-Karp) on the same literal graph. ``test_planted_mistakes`` compiles the
 oracle with one deliberate error at a time and shows that the pins catch it.
 """
 import os
@@ -275,3 +276,62 @@ def test_certificate_rejects_broken_states():
     wrong = top.copy()
     wrong[0, 0] = (wrong[0, 0] + 1) % 6
     assert oracle.certify(cost, d, a, st, value, wrong) == 14
+
+
+def _literal_graph_csr(cost, delta, alpha, inf):
+    """The s-t graph of Section 1.2 as a scipy CSR capacity matrix (parallel arcs summed):
+    node weights w(z) = c(z) - c(z-1), w(x,y,0) = c(x,y,0), w(0,0,0) -= 1 + sum c(.,.,0);
+    s->v with -w for w < 0, v->t with w for w > 0; `inf` arcs down the column and to
+    (x',y',max(0,z-delta)) for every 4-neighbour; alpha arcs both ways between neighbours."""
+    import scipy.sparse as sp
+
+    X, Y, Z = cost.shape
+    c = cost.astype(np.int64)
+    w = np.diff(c, axis=2, prepend=0)
+    w[:, :, 0] = c[:, :, 0]
+    w[0, 0, 0] -= 1 + c[:, :, 0].sum()
+    idx = lambda x, y, z: (x * Y + y) * Z + z  # noqa: E731
+    n = X * Y * Z
+    s, t = n, n + 1
+    rows, cols, caps = [], [], []
+
+    def arc(a, b, cap):
+        rows.append(a)
+        cols.append(b)
+        caps.append(cap)
+
+    for x in range(X):
+        for y in range(Y):
+            for z in range(Z):
+                v = idx(x, y, z)
+                if w[x, y, z] < 0:
+                    arc(s, v, -w[x, y, z])
+                elif w[x, y, z] > 0:
+                    arc(v, t, w[x, y, z])
+                if z >= 1:
+                    arc(v, idx(x, y, z - 1), inf)
+                for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                    x2, y2 = x + dx, y + dy
+                    if 0 <= x2 < X and 0 <= y2 < Y:
+                        arc(v, idx(x2, y2, max(0, z - delta)), inf)
+                        if alpha > 0:
+                            arc(v, idx(x2, y2, z), alpha)
+    return sp.csr_matrix((np.array(caps, dtype=np.int32), (rows, cols)), shape=(n + 2, n + 2)), s, t
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dinic_matches_library_edmonds_karp(seed):
+    """The oracle's Dinic against scipy's Edmonds-Karp max-flow on the same literal graph
+    (a different algorithm from a library; small costs keep every capacity in int32)."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    rng = np.random.default_rng(700 + seed)
+    X, Y, Z = (int(v) for v in rng.integers(2, 6, size=3))
+    delta, alpha = int(rng.integers(0, Z + 1)), int(rng.integers(0, 6))
+    cost = _rand_cost(rng, X, Y, Z, lo=-15, hi=30)
+    if cost[:, :, 0].sum() > 1000:
+        cost[:, :, 0] //= 4
+    inf = 1 << 28
+    g, s, t = _literal_graph_csr(cost, delta, alpha, inf)
+    ref = csgraph.maximum_flow(g, s, t, method="edmonds_karp").flow_value
+    assert ref < inf  # no infinite path from s to t
+    assert oracle.solve(cost, delta, alpha).flow == ref
