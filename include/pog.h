@@ -74,6 +74,7 @@ typedef struct {
 #define POG_FLAG_TIMING 2     /* time each kernel family with CUDA events on the graph's stream */
 #define POG_FLAG_NO_PREPUSH 4 /* skip the column pre-push along the down arcs */
 #define POG_FLAG_NODE_SWEEPS 8 /* node-parallel sweeps instead of shared-memory tiles */
+#define POG_FLAG_NO_TMA 16    /* load shared-memory tiles word by word, not by bulk tensor copies */
 
 /* Counters of the last pog_maxflow. */
 typedef struct {
@@ -293,9 +294,11 @@ POG_API pog_status pog_solve_batch_f32(int32_t B, const float *cost_dev, float s
  * Blocks until the stream has finished the solve. Allocates no device or host memory,
  * creates no events and calls no allocating library routine.
  *
- * Set-up: the first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call before any
- * stream capture begins on the device.
+ * Set-up: every call looks up the array's device address with cudaGetSymbolAddress
+ * (with the device current), so no address outlives the context it came from. The first
+ * call on a device also loads the library's device code there, which places the array
+ * in that device's memory; make that first call before any stream capture begins on the
+ * device.
  *
  * Sharing: every call on a device uses the same array, which keeps the last call's
  * contents (each call clears what must start at zero). Calls whose device work

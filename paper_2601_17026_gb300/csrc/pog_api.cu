@@ -290,15 +290,20 @@ template <class Launch>
 pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, void *stream, pog_graph **out,
                        Launch launch) {
     if (!out || n < 1 || n > pog::kMaxVolumes) return POG_E_INVALID;
-    long long total = 0, soft_total = 0, cols = 0;
+    // Every volume starts at a multiple of kNodeAlign nodes in the union arrays (and in the
+    // soft-arc arrays), so its arrays are aligned for bulk tensor copies and its visited
+    // bits start on a word boundary; the padding nodes belong to no volume.
+    long long total = 0, padded = 0, soft_padded = 0, cols = 0;
     for (int v = 0; v < n; ++v) {
         if (!valid_volume(spec[v])) return POG_E_INVALID;
         const long long N = (long long)spec[v].X * spec[v].Y * spec[v].Z;
+        const long long Np = (N + pog::kNodeAlign - 1) / pog::kNodeAlign * pog::kNodeAlign;
         total += N;
-        if (spec[v].alpha > 0) soft_total += N;
+        padded += Np;
+        if (spec[v].alpha > 0) soft_padded += Np;
         cols += (long long)spec[v].X * spec[v].Y;
     }
-    if (total >= (1ll << 31) - 64) return POG_E_INVALID;
+    if (padded >= (1ll << 31) - 64) return POG_E_INVALID;
     pog_graph *g = new (std::nothrow) pog_graph();
     if (!g) return POG_E_NOMEM;
     g->nvol = n;
@@ -309,7 +314,7 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->alpha = spec[0].alpha;
     g->N = (long long)g->X * g->Y * g->Z;
     g->n_total = total;
-    g->any_soft = soft_total > 0;
+    g->any_soft = soft_padded > 0;
     g->stream = static_cast<cudaStream_t>(stream);
     set_options(g, opt);
     g->vols = new (std::nothrow) Grid[n]();
@@ -336,12 +341,15 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
         d.Y = spec[v].Y;
         d.Z = spec[v].Z;
         tiles += pog::tile_count(d, g->tile_shape);
-        g->node_base[v + 1] = g->node_base[v] + spec[v].X * spec[v].Y * spec[v].Z;
+        const int N = spec[v].X * spec[v].Y * spec[v].Z;
+        g->node_base[v + 1] = g->node_base[v] + (N + pog::kNodeAlign - 1) / pog::kNodeAlign * pog::kNodeAlign;
         g->tile_base[v + 1] = (int)tiles;
         g->col_base[v + 1] = g->col_base[v] + (long long)spec[v].X * spec[v].Y;
     }
-    const size_t per = align_up((size_t)total * sizeof(int32_t), 256);
-    const size_t per_soft = align_up((size_t)soft_total * sizeof(int32_t), 256);
+    const size_t per = align_up((size_t)padded * sizeof(int32_t), 256);
+    const size_t per_soft = align_up((size_t)soft_padded * sizeof(int32_t), 256);
+    const size_t visit = align_up((size_t)padded / 8, 256);
+    const size_t tmaps = align_up((size_t)n * pog::kTileArrays * pog::kTensorMapBytes, 256);
     const size_t heights = align_up((size_t)cols * sizeof(int32_t), 256);
     const size_t ctr = align_up(sizeof(DevCounters), 256) + (size_t)kGapLevels / 8;
     const size_t vctr = align_up(sizeof(DevCounters) * n, 256);
@@ -349,13 +357,19 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     const size_t trace = sizeof(pog::LevelTrace) * pog::kTraceLevels;
     const size_t tile_bytes = align_up(sizeof(int32_t) * (size_t)tiles, 256);
     const size_t table = 2 * (align_up(sizeof(Grid) * n, 256) + 2 * align_up(sizeof(int) * (n + 1), 256));
-    g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 4 * tile_bytes + 256 + table;
+    g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 4 * tile_bytes + 256 + table +
+                     visit + tmaps;
     cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g->arena = nullptr;
         pog_free(g);
         return e == cudaErrorMemoryAllocation ? POG_E_NOMEM : POG_E_CUDA;
+    }
+    g->tmap_host = std::calloc((size_t)n * pog::kTileArrays, pog::kTensorMapBytes);
+    if (!g->tmap_host) {
+        pog_free(g);
+        return POG_E_NOMEM;
     }
     e = cudaHostAlloc(reinterpret_cast<void **>(&g->ctr_host), sizeof(DevCounters) * (n + 1), cudaHostAllocDefault);
     if (e != cudaSuccess) {
@@ -398,6 +412,8 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->live_node_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
     g->live_tile_base_dev = reinterpret_cast<int *>(take(align_up(sizeof(int) * (n + 1), 256)));
     g->ctr = reinterpret_cast<DevCounters *>(take(ctr));
+    g->visit = reinterpret_cast<unsigned *>(take(visit));
+    g->tmap_dev = take(tmaps);
     long long soft_off = 0;
     for (int v = 0; v < n; ++v) {
         Grid &gr = g->vols[v];
@@ -407,16 +423,21 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
         gr.Z = spec[v].Z;
         gr.delta = spec[v].delta;
         gr.alpha = spec[v].alpha;
-        gr.N = g->node_base[v + 1] - g->node_base[v];
+        gr.N = spec[v].X * spec[v].Y * spec[v].Z;  // the padding after it belongs to no volume
         gr.lab = arr[0] + off;
         gr.exc = arr[1] + off;
         gr.snk = arr[2] + off;
         gr.fdn = arr[3] + off;
         for (int d = 0; d < 4; ++d) gr.fh[d] = arr[4 + d] + off;
         for (int k = 0; k < 2; ++k) gr.gs[k] = spec[v].alpha > 0 ? soft[k] + soft_off : nullptr;
-        if (spec[v].alpha > 0) soft_off += gr.N;
+        if (spec[v].alpha > 0) soft_off += g->node_base[v + 1] - g->node_base[v];
         gr.ctr = g->vctr + v;
         gr.trace = nullptr;
+        char *host_maps = static_cast<char *>(g->tmap_host) + (size_t)v * pog::kTileArrays * pog::kTensorMapBytes;
+        const bool maps = !(g->flags & POG_FLAG_NO_TMA) && !(g->flags & POG_FLAG_NODE_SWEEPS) &&
+                          pog::encode_tile_maps(gr, g->tile_shape, host_maps);
+        gr.tmap = maps ? static_cast<char *>(g->tmap_dev) + (size_t)v * pog::kTileArrays * pog::kTensorMapBytes
+                       : nullptr;
     }
     g->grid = g->vols[0];
     g->batch.vols = g->vols_dev;
@@ -426,7 +447,10 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->batch.n_total = (int)total;
     g->batch.ctr = g->ctr;
     g->batch.trace = g->trace;
-    e = cudaMemcpyAsync(g->vols_dev, g->vols, sizeof(Grid) * n, cudaMemcpyHostToDevice, g->stream);
+    g->batch.visit = g->visit;
+    e = cudaMemcpyAsync(g->tmap_dev, g->tmap_host, (size_t)n * pog::kTileArrays * pog::kTensorMapBytes,
+                        cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->vols_dev, g->vols, sizeof(Grid) * n, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->node_base_dev, g->node_base, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess)
@@ -597,6 +621,7 @@ void pog_free(pog_graph *g) {
         if (ev) cudaEventDestroy(ev);
     if (g->arena) cudaFree(g->arena);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
+    std::free(g->tmap_host);
     delete[] g->vols;
     delete[] g->node_base;
     delete[] g->tile_base;

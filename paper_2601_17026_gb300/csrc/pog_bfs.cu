@@ -9,9 +9,11 @@
 //   cut extraction (forward BFS): marks = nodes reachable in the residual graph from the
 //     nodes that hold excess, i.e. the source side of the minimal minimum cut.
 //
-// Frontier appends are warp-aggregated; a node joins a frontier once, through an
-// atomicCAS on its label. The grid barrier spins with an iteration limit; on timeout it
-// raises POG_ERR_TIMEOUT and every block leaves.
+// Frontier appends are warp-aggregated. In the global relabel a node joins a frontier
+// once, through an atomicOr on its bit of a visited bitmap (one bit per node, 1/32 of the
+// label array, so it stays in L2 while the labels do not); the cut extraction claims
+// nodes by an atomicCAS on their mark. The grid barrier spins with an iteration limit; on
+// timeout it raises POG_ERR_TIMEOUT and every block leaves.
 #include <cooperative_groups.h>
 
 #include "pog_internal.cuh"
@@ -91,10 +93,13 @@ __device__ __forceinline__ void decode(const Grid &g, int u, int &x, int &y, int
     y = col - x * g.Y;
 }
 
+// In-arcs of v with their residuals; h.lab receives the visited-bitmap word of each tail
+// (union index base + node), or all bits set for an absent arc.
 template <bool RO>
-__device__ __forceinline__ void gather_in_any(const Grid &g, int v, int x, int y, int z, Hood &h) {
-    if (g.gs[0]) gather_in<true, RO>(g, v, x, y, z, h);
-    else gather_in<false, RO>(g, v, x, y, z, h);
+__device__ __forceinline__ void gather_in_any(const Grid &g, int v, int x, int y, int z, Hood &h,
+                                              const unsigned *visit, int base) {
+    if (g.gs[0]) gather_in<true, RO>(g, v, x, y, z, h, visit, base);
+    else gather_in<false, RO>(g, v, x, y, z, h, visit, base);
 }
 
 template <bool RO>
@@ -159,28 +164,40 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
     // residual, level 2 the others with a residual arc into level 1 (read off the far
     // ends' sink residuals, which no step of the search changes); everything else starts
     // unreachable. Only level 2 is queued.
+    // The warps cover aligned runs of 32 nodes (volume bases are multiples of 64 nodes), so
+    // each writes whole words of the visited bitmap: bits of levels 1 and 2, and of the
+    // bottom layer, which no search step may claim.
     int ones = 0;
+    const int lane = threadIdx.x & 31;
+    unsigned *visit = b.visit;
     for (int v = 0; v < b.nvol; ++v) {
         const Grid g = SINGLE ? g0 : b.vols[v];
         const int base = sbase[v];
         unvisited += (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
-        for (int u = tid; u < g.N; u += stride) {
-            int x, y, z;
-            decode(g, u, x, y, z);
+        for (int u0 = tid - lane; u0 < g.N; u0 += stride) {
+            const int u = u0 + lane;
             int l = POG_INF;
-            if (z != 0) {
-                if (__ldg(g.snk + u) > 0) {
-                    l = 1;
-                } else {
-                    Hood hd;
-                    gather_out_any<true>(g, u, x, y, z, hd, g.snk);
-                    bool hit = false;
+            bool bottom = false;
+            if (u < g.N) {
+                int x, y, z;
+                decode(g, u, x, y, z);
+                bottom = z == 0;
+                if (!bottom) {
+                    if (__ldg(g.snk + u) > 0) {
+                        l = 1;
+                    } else {
+                        Hood hd;
+                        gather_out_any<true>(g, u, x, y, z, hd, g.snk);
+                        bool hit = false;
 #pragma unroll
-                    for (int k = 0; k < kMaxArcs; ++k) hit |= hd.res[k] > 0 && hd.lab[k] > 0;
-                    if (hit) l = 2;
+                        for (int k = 0; k < kMaxArcs; ++k) hit |= hd.res[k] > 0 && hd.lab[k] > 0;
+                        if (hit) l = 2;
+                    }
                 }
+                g.lab[u] = l;
             }
-            g.lab[u] = l;
+            const unsigned seen = __ballot_sync(0xffffffffu, bottom || l < POG_INF);
+            if (lane == 0) visit[(base + u0) >> 5] = seen;
             ones += l == 1;
             if (l == 2) warp_append(base + u, qb, &s->size[2]);
         }
@@ -216,13 +233,19 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
             for (int vi = 0; vi < b.nvol; ++vi) {
                 const Grid g = SINGLE ? g0 : b.vols[vi];
                 const int base = sbase[vi];
-                for (int u = tid; u < g.N; u += stride) {
-                    if (ldcg(g.lab + u) != POG_INF) continue;
-                    int x, y, z;
-                    decode(g, u, x, y, z);
-                    if (z == 0) continue;
-                    const bool hit = g.gs[0] ? bottom_up_hit<true>(g, u, x, y, z, level)
-                                             : bottom_up_hit<false>(g, u, x, y, z, level);
+                for (int u0 = tid - lane; u0 < g.N; u0 += stride) {
+                    const int u = u0 + lane;
+                    const unsigned seen = ldcg(reinterpret_cast<const int32_t *>(visit) + ((base + u0) >> 5));
+                    if (seen == 0xffffffffu) continue;  // the whole run is labelled (warp-uniform)
+                    bool hit = false;
+                    if (u < g.N && !((seen >> lane) & 1u)) {
+                        int x, y, z;
+                        decode(g, u, x, y, z);
+                        hit = g.gs[0] ? bottom_up_hit<true>(g, u, x, y, z, level)
+                                      : bottom_up_hit<false>(g, u, x, y, z, level);
+                    }
+                    const unsigned won = __ballot_sync(0xffffffffu, hit);
+                    if (won && lane == 0) atomicOr(visit + ((base + u0) >> 5), won);
                     if (hit) {
                         g.lab[u] = level + 1;
                         warp_append(base + u, nxt, &s->size[(level + 1) % 3]);
@@ -245,17 +268,24 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
                     const int v = uv - base;
                     int x, y, z;
                     decode(g, v, x, y, z);
-                    gather_in_any<true>(g, v, x, y, z, hd);
-                    int old[kMaxArcs];
-#pragma unroll
-                    for (int k = 0; k < kMaxArcs; ++k)
-                        old[k] = (hd.res[k] > 0 && hd.lab[k] == POG_INF)
-                                     ? atomicCAS(g.lab + hd.node[k], POG_INF, level + 1)
-                                     : 0;
+                    // residuals of the in-arcs and the visited words of their tails, in one
+                    // round trip (the words come from the bitmap in L2, not from the labels)
+                    gather_in_any<true>(g, v, x, y, z, hd, visit, base);
+                    unsigned old[kMaxArcs];
 #pragma unroll
                     for (int k = 0; k < kMaxArcs; ++k) {
-                        if (hd.res[k] > 0 && hd.lab[k] == POG_INF && old[k] == POG_INF) won |= 1u << k;
-                        hd.node[k] += base;  // to union indices
+                        const int un = base + hd.node[k];
+                        const unsigned bit = 1u << (un & 31);
+                        old[k] = (hd.res[k] > 0 && !(hd.lab[k] & bit)) ? atomicOr(visit + (un >> 5), bit) : bit;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kMaxArcs; ++k) {
+                        const int un = base + hd.node[k];
+                        if (!(old[k] & (1u << (un & 31)))) {
+                            won |= 1u << k;
+                            g.lab[hd.node[k]] = level + 1;
+                        }
+                        hd.node[k] = un;  // to union indices
                     }
                 }
                 warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);

@@ -76,7 +76,18 @@ struct Grid {
     int32_t *gs[2];        // net soft flow towards x+1 / y+1
     DevCounters *ctr;
     LevelTrace *trace;     // per-level trace of the global relabel (may be null)
+    const void *tmap;      // device: tensor maps of the tile arrays (kTileArrays of them, in
+                           // the order of the shared tile image), or null: plain tile loads
 };
+
+// Arrays of a shared-memory tile image, in image order: lab, exc, snk, fdn, fh[0..3],
+// gs[0..1] (the last two only with soft arcs).
+constexpr int kTileArrays = 10;
+constexpr int kTensorMapBytes = 128;
+
+// Volumes of a batch start at multiples of this many nodes in the union arrays, so every
+// volume's arrays are 256-byte aligned (tensor-map and visited-bitmap word alignment).
+constexpr int kNodeAlign = 64;
 
 // A batch of independent volumes solved as one graph: the disjoint union of their
 // graphs (they share only s and t), so one launch of each kernel serves all of them.
@@ -93,6 +104,7 @@ struct Batch {
     int n_total;
     DevCounters *ctr;      // union counters: active nodes, BFS levels, gap, tile visits, timeouts
     LevelTrace *trace;     // per-level trace of the last global relabel (may be null)
+    unsigned *visit;       // global relabel: one bit per union node, set once it is labelled
 };
 
 // Largest v with base[v] <= idx (base ascending, base[0] = 0, nvol entries searched).
@@ -221,9 +233,12 @@ __device__ __forceinline__ bool out_arc(const Grid &g, int u, int x, int y, int 
 }
 
 // In-arcs of v (arcs u -> v): slot 0 from above, 1 from below, 2+3d hard arc of
-// (q, z+D), 3+3d reverse of v's hard arc, 4+3d soft.
+// (q, z+D), 3+3d reverse of v's hard arc, 4+3d soft. With `visit`, h.lab receives the
+// visited-bitmap word of each tail (union node base + u) instead of its label, all bits
+// set for an absent arc.
 template <bool SOFT, bool RO = false>
-__device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, int z, Hood &h) {
+__device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, int z, Hood &h,
+                                          const unsigned *visit = nullptr, int base = 0) {
 #pragma unroll
     for (int i = 0; i < kMaxArcs; ++i) {
         h.res[i] = 0;
@@ -256,6 +271,15 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
             h.node[4 + 3 * d] = u;
             h.res[4 + 3 * d] = (d & 1) ? g.alpha + ld_arc<RO>(g.gs[d >> 1] + v) : g.alpha - ld_arc<RO>(g.gs[d >> 1] + u);
         }
+    }
+    if (visit) {
+#pragma unroll
+        for (int i = 0; i < kMaxArcs; ++i)
+            h.lab[i] = ldcg(reinterpret_cast<const int32_t *>(visit) + ((base + h.node[i]) >> 5));
+#pragma unroll
+        for (int i = 0; i < kMaxArcs; ++i)
+            if (h.res[i] <= 0) h.lab[i] = -1;
+        return;
     }
 #pragma unroll
     for (int i = 0; i < kMaxArcs; ++i) h.lab[i] = ldcg(g.lab + h.node[i]);
@@ -301,6 +325,9 @@ struct pog_graph {
     pog::DevCounters *ctr;       // device: union counters
     pog::DevCounters *vctr;      // device [nvol]: per-volume counters
     pog::DevCounters *ctr_host;  // pinned host mirror of ctr followed by vctr
+    unsigned *visit;             // device [padded nodes / 32]: visited bits of the global relabel
+    void *tmap_host;             // host [nvol][kTileArrays]: tensor maps of the tile arrays
+    void *tmap_dev;              // device copy of tmap_host
     int solved;
     long long flow;              // volume 0
     long long *flows;            // host [nvol]

@@ -498,7 +498,8 @@ cudaError_t launch_sweep(const Batch &b, int *list, int *count, int ops, cudaStr
 }
 
 cudaError_t launch_gap(const Batch &b, unsigned int *bits, int levels, cudaStream_t st) {
-    cudaMemsetAsync(bits, 0, (size_t)(levels / 32) * sizeof(unsigned int), st);
+    const cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)(levels / 32) * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
     const int blocks = grid_blocks();
     k_gap_occupancy<<<blocks, kThreads, 0, st>>>(b, bits, levels);
     k_gap_find<<<1, 1024, 0, st>>>(b, bits, levels);

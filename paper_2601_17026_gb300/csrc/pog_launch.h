@@ -28,6 +28,11 @@ cudaError_t launch_cut_reach(const Batch &b, const Grid *single, int *qa, int *q
 constexpr int kTileShapes = 4;
 long long tile_count(const Grid &g, int shape);
 long long tile_count_max(const Grid &g);
+// Encode the tensor maps of a volume's tile arrays (kTileArrays x kTensorMapBytes bytes,
+// host memory at `out`) for the boxes of tile shape `shape`; false when the volume cannot
+// use bulk tensor copies (z extent not a multiple of 4, an unaligned array, no driver
+// support), in which case the tile kernel loads words one by one.
+bool encode_tile_maps(const Grid &g, int shape, void *out);
 // `tiles`: 4 arrays of `ntiles` ints (flag and list of two alternating sweep lists, all
 // flags zero at the start); `work`: 6 ints, zero at the start. `serial` counts the
 // tiled sweeps run on these buffers; `full_scan` is set on the first sweep after each

@@ -3,7 +3,6 @@
 // array instead of memory from cudaMalloc. See include/pog.h for the contract.
 #include <cstddef>
 #include <cstring>
-#include <mutex>
 
 #include "pog.h"
 #include "pog_internal.cuh"
@@ -12,7 +11,7 @@
 namespace {
 
 // The scratch array. In host code its name is only a stand-in for the device object:
-// its device address comes from cudaGetSymbolAddress (once per device, below).
+// its device address comes from cudaGetSymbolAddress (on every call, below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[POG_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kGapLevels = 1 << 20;        // labels tracked by the gap bitmap
@@ -20,12 +19,8 @@ constexpr int kSweepsPerRelabel = 64;      // fixed: this path keeps no timing e
 constexpr int kTileSweeps = 8;
 constexpr int kNodeOps = 4;
 constexpr int kMaxRounds = 1 << 20;
-constexpr int kMaxDevices = 64;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-std::mutex g_symbol_lock;
-void *g_symbol_addr[kMaxDevices] = {nullptr};
 
 pog_status from_cuda(cudaError_t e) { return e == cudaSuccess ? POG_OK : POG_E_CUDA; }
 
@@ -40,19 +35,14 @@ pog_status from_cuda(cudaError_t e) { return e == cudaSuccess ? POG_OK : POG_E_C
         if (_s != POG_OK) return _s;                     \
     } while (0)
 
-// Device address of the scratch array on the current device (set up on first use).
+// Device address of the scratch array in the current device's context. Looked up on every
+// call, so a context created anew (after cudaDeviceReset) is never given a stale address;
+// once the module is loaded in a context the lookup allocates nothing.
 pog_status scratch_address(void **out) {
-    int dev = 0;
-    NA_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return POG_E_INVALID;
-    std::lock_guard<std::mutex> lock(g_symbol_lock);
-    if (!g_symbol_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return POG_E_CUDA;
-        g_symbol_addr[dev] = p;
-    }
-    *out = g_symbol_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return POG_E_CUDA;
+    *out = p;
     return POG_OK;
 }
 
@@ -77,7 +67,7 @@ size_t scratch_bytes(int X, int Y, int Z, int alpha) {
     dims.Y = Y;
     dims.Z = Z;
     const size_t tiles = (size_t)pog::tile_count_max(dims);
-    return (arrays + 2) * align_up(N * 4, 256) + align_up(4 * tiles * 4, 256) + 256 +
+    return (arrays + 2) * align_up(N * 4, 256) + align_up((N + 31) / 32 * 4, 256) + align_up(4 * tiles * 4, 256) + 256 +
            align_up(sizeof(pog::BfsSync), 256) + 2 * align_up(sizeof(pog::DevCounters), 256) + kGapLevels / 8 +
            align_up(sizeof(pog::Grid), 256) + 2 * 256;
 }
@@ -131,6 +121,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     for (auto &s : g.gs) s = alpha > 0 ? c.take<int32_t>(N * 4) : nullptr;
     int32_t *queue_a = c.take<int32_t>(N * 4);
     int32_t *queue_b = c.take<int32_t>(N * 4);
+    unsigned *visit = c.take<unsigned>((N + 31) / 32 * 4);  // the relabel's visited bits (written by it)
     const size_t tiles = (size_t)pog::tile_count_max(g);
     const int shape = (opt && opt->tile_shape > 0 && opt->tile_shape < pog::kTileShapes) ? opt->tile_shape : 0;
     const int bu_ratio = !opt || opt->bfs_bottom_up_ratio == 0 ? 8 : (opt->bfs_bottom_up_ratio < 0 ? 0 : opt->bfs_bottom_up_ratio);
@@ -152,6 +143,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     b.n_total = (int)N;
     b.ctr = uctr;
     b.trace = nullptr;
+    b.visit = visit;
     const int bases[2] = {0, (int)N};
     const int tbases[2] = {0, (int)pog::tile_count(g, shape)};
 

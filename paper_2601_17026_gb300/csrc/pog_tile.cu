@@ -14,6 +14,16 @@
 // concurrent pushes (they add flow in the reverse direction, or excess), so a stale read
 // never lets a tile push more than is there and the preflow stays valid, as in the node
 // kernels; a stale label of a neighbour (too low) can cost convergence, never validity.
+//
+// Tile loads: when the volume has tensor maps (z extent a multiple of 4, arrays 16-byte
+// aligned), one thread issues one bulk tensor copy (cp.async.bulk.tensor, TMA) per state
+// array, a 3-D box of TX x TY x TZ int32 straight into the shared image, all completing on
+// one mbarrier; out-of-volume box elements arrive as zeros and are then set to the values
+// of a node outside the graph. Otherwise every thread loads its nodes' words one by one.
+#include <cuda.h>
+
+#include <cstring>
+
 #include "pog_internal.cuh"
 #include "pog_launch.h"
 
@@ -25,6 +35,7 @@ constexpr int kTileNodes = 1024;  // nodes per tile, every shape
 constexpr int kTileThreads = 256;
 constexpr int kPerThread = kTileNodes / kTileThreads;  // 4
 constexpr int kTileBlocksPerSm = 4;                 // resident tile visits per SM
+constexpr long long kTmaSpinLimit = 1ll << 22;      // polls of a tile load's mbarrier before giving up
 
 // Tile shapes (columns in x, columns in y, heights), all of 1024 nodes. Node s of a tile
 // sits at column c = s / TZ, height z0 + s % TZ, so consecutive threads read
@@ -87,14 +98,45 @@ __global__ void __launch_bounds__(256) k_clear_listed(int *flag, const int *list
 // a visit makes to a word that other tiles may also change (excess and arc words) is
 // applied to the global copy at once as well (fire-and-forget atomics), so the image
 // only serves reads; the owner-only words (label, sink residual) are stored at the end.
+// The arrays follow one another in the order of the tensor maps (kTileArrays), each the
+// target of one bulk tensor copy.
 struct TileSmem {
     int lab[kTileNodes], exc[kTileNodes], snk[kTileNodes], fdn[kTileNodes];
     int fh[4][kTileNodes];
-    unsigned nb;  // neighbour tiles pushed into: bit (dx+1)*9 + (dy+1)*3 + (dz+1)
 };
 struct TileSoft {
     int gs[2][kTileNodes];
 };
+static_assert(sizeof(TileSmem) == 8 * 4 * kTileNodes, "tile image arrays must be contiguous");
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// One bulk tensor copy of a 3-D box (coordinates z, y, x of its first element) into
+// shared memory, completing on `bar` with its byte count.
+__device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int z, int y, int x, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(z), "r"(y), "r"(x), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Wait for phase `parity` of an mbarrier, with an iteration limit; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    for (long long i = 0; i < kTmaSpinLimit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // Lists of a tiled sweep: the tiles to visit now, and the next sweep's tiles (those a
 // visit leaves active, and those that receive a push across their boundary).
@@ -112,9 +154,11 @@ struct TileLists {
 // One visit of one tile: stage it in shared memory, run the local sweeps, write it back.
 // `g` is the tile's volume, `tile` its union index (for the listing flags), `local_tile`
 // its index within the volume.
+// Returns false when the block must stop (a tile load's wait gave up; the error word is set).
 template <int TX, int TY, int TZ, bool SOFT>
-__device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int tile, int local_tile,
-                                           const TileLists &L, int local_sweeps, TileSmem &S, TileSoft &SS) {
+__device__ __forceinline__ bool tile_visit(const Grid &g, const Batch &b, int tile, int local_tile,
+                                           const TileLists &L, int local_sweeps, TileSmem &S, TileSoft &SS,
+                                           unsigned &nbmask, uint64_t *bar, unsigned &phase) {
     const bool soft = SOFT && g.gs[0] != nullptr;
     const int nty = (g.Y + TY - 1) / TY, ntz = (g.Z + TZ - 1) / TZ;
     const int tz = local_tile % ntz;
@@ -122,31 +166,79 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
     const int x0 = (txy / nty) * TX, y0 = (txy % nty) * TY, z0 = tz * TZ;
     if (threadIdx.x == 0) {
         L.flag[tile] = 0;  // this sweep's listing is consumed
-        S.nb = 0;
+        nbmask = 0;
     }
 
     // ---- load (coalesced along z)
-    int node[kPerThread];
-    bool own[kPerThread];
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-        const int s = threadIdx.x + kTileThreads * k;
+    // Node of tile place s, and whether the tile owns it (inside the volume, above the
+    // bottom layer); recomputed where needed rather than kept live through the sweeps.
+    auto node_of = [&](int s, bool &own) {
         const int c = s / TZ;  // column within the tile
         const int x = x0 + c / TY, y = y0 + c % TY, z = z0 + s % TZ;
-        own[k] = x < g.X && y < g.Y && z < g.Z && z >= 1;
-        node[k] = own[k] ? (x * g.Y + y) * g.Z + z : -1;
-        const int u = node[k];
-        S.lab[s] = own[k] ? ldcg(g.lab + u) : POG_INF;
-        const int e = own[k] ? ldcg(g.exc + u) : 0;
-        if (e < 0) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes
-        S.exc[s] = e;
-        S.snk[s] = own[k] ? ldcg(g.snk + u) : 0;
-        S.fdn[s] = own[k] ? ldcg(g.fdn + u) : 0;
+        own = x < g.X && y < g.Y && z < g.Z && z >= 1;
+        return (x * g.Y + y) * g.Z + z;
+    };
+    if (g.tmap) {
+        // bulk tensor copies: one box per array, issued by one thread; the block waits on
+        // the mbarrier (the previous visit's shared-memory accesses are ordered before the
+        // copies' writes by the proxy fence after the block barrier that ended that visit)
+        const int narr = soft ? kTileArrays : kTileArrays - 2;
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                         "r"(narr * kTileNodes * 4)
+                         : "memory");
+            const char *maps = static_cast<const char *>(g.tmap);
+            int *dst = S.lab;
+#pragma unroll 1
+            for (int a = 0; a < narr; ++a)
+                tma_load_box(dst + a * kTileNodes, maps + a * kTensorMapBytes, z0, y0, x0, bar);
+        }
+        bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(&g.ctr->error, POG_ERR_TIMEOUT);
+            mbar_wait(bar, phase);  // let copies still in flight land before the block leaves
+            return false;
+        }
+        phase ^= 1u;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) S.fh[d][s] = own[k] ? ldcg(g.fh[d] + u) : 0;
-        if (soft) {
+        for (int k = 0; k < kPerThread; ++k) {
+            const int s = threadIdx.x + kTileThreads * k;
+            bool own;
+            node_of(s, own);
+            if (!own) {  // outside the volume, or the bottom layer: a node outside the graph
+                S.lab[s] = POG_INF;
+                S.exc[s] = 0;
+                S.snk[s] = 0;
+                S.fdn[s] = 0;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) SS.gs[j][s] = own[k] ? ldcg(g.gs[j] + u) : 0;
+                for (int d = 0; d < 4; ++d) S.fh[d][s] = 0;
+                if (soft) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) SS.gs[j][s] = 0;
+                }
+            } else if (S.exc[s] < 0) {
+                atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int s = threadIdx.x + kTileThreads * k;
+            bool own;
+            const int u = node_of(s, own);
+            S.lab[s] = own ? ldcg(g.lab + u) : POG_INF;
+            const int e = own ? ldcg(g.exc + u) : 0;
+            if (e < 0) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes
+            S.exc[s] = e;
+            S.snk[s] = own ? ldcg(g.snk + u) : 0;
+            S.fdn[s] = own ? ldcg(g.fdn + u) : 0;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) S.fh[d][s] = own ? ldcg(g.fh[d] + u) : 0;
+            if (soft) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) SS.gs[j][s] = own ? ldcg(g.gs[j] + u) : 0;
+            }
         }
     }
     __syncthreads();
@@ -325,7 +417,7 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
                     const int mx = tcx < 0 ? 0 : (tcx < TX ? 1 : 2);
                     const int my = tcy < 0 ? 0 : (tcy < TY ? 1 : 2);
                     const int mz = tcz < 0 ? 0 : (tcz < TZ ? 1 : 2);
-                    atomicOr(&S.nb, 1u << (mx * 9 + my * 3 + mz));
+                    atomicOr(&nbmask, 1u << (mx * 9 + my * 3 + mz));
                 } else {  // a vertical offset longer than a tile
                     list_tile(tile - local_tile + (((x0 + tcx) / TX) * nty + (y0 + tcy) / TY) * ntz + (z0 + tcz) / TZ,
                               L.nflag, L.nlist, L.ncount);
@@ -338,10 +430,12 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
 #pragma unroll
     for (int k = 0; k < kPerThread; ++k) {
         const int s = threadIdx.x + kTileThreads * k;
-        still |= own[k] && S.exc[s] > 0 && S.lab[s] < POG_INF;
+        bool own;
+        node_of(s, own);
+        still |= own && S.exc[s] > 0 && S.lab[s] < POG_INF;
     }
     const unsigned keep = __syncthreads_or(still) ? 1u << 13 : 0u;  // bit 13, (dx, dy, dz) = 0: this tile
-    if (threadIdx.x < 27 && (((S.nb | keep) >> threadIdx.x) & 1u)) {
+    if (threadIdx.x < 27 && (((nbmask | keep) >> threadIdx.x) & 1u)) {
         const int t = threadIdx.x;
         const int nx = txy / nty + t / 9 - 1, ny = txy % nty + (t / 3) % 3 - 1, nz = tz + t % 3 - 1;
         list_tile(tile - local_tile + (nx * nty + ny) * ntz + nz, L.nflag, L.nlist, L.ncount);
@@ -351,11 +445,14 @@ __device__ __forceinline__ void tile_visit(const Grid &g, const Batch &b, int ti
     // ---- write back the owner-only words
 #pragma unroll
     for (int k = 0; k < kPerThread; ++k) {
-        if (!own[k]) continue;
         const int s = threadIdx.x + kTileThreads * k;
-        g.lab[node[k]] = S.lab[s];
-        g.snk[node[k]] = S.snk[s];
+        bool own;
+        const int u = node_of(s, own);
+        if (!own) continue;
+        g.lab[u] = S.lab[s];
+        g.snk[u] = S.snk[s];
     }
+    return true;
 }
 
 // SOFT: the shared image has room for soft arcs (some volume of the batch has alpha > 0);
@@ -365,14 +462,24 @@ template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
 __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSm) k_tile_push_relabel(Batch b, Grid g0, int tile_base0, TileLists L,
                                                                     int local_sweeps) {
     extern __shared__ int4 smem_raw[];
-    TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
-    TileSoft &SS = *reinterpret_cast<TileSoft *>(reinterpret_cast<char *>(smem_raw) + sizeof(TileSmem));
+    // the image starts on a 128-byte boundary (bulk tensor copy destinations)
+    char *img = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    TileSmem &S = *reinterpret_cast<TileSmem *>(img);
+    TileSoft &SS = *reinterpret_cast<TileSoft *>(img + sizeof(TileSmem));
     __shared__ int tile_id, local_tile;
     __shared__ Grid sg;
+    __shared__ unsigned nbmask;  // neighbour tiles pushed into: bit (dx+1)*9 + (dy+1)*3 + (dz+1)
+    __shared__ uint64_t bar;     // completion of a visit's bulk tile copies
+    unsigned phase = 0;
     const int ntiles = *L.count;
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // last read by the previous sweep
         L.zero[0] = 0;
         L.zero[1] = 0;
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (SINGLE) sg = g0;  // the view in shared memory, not a local copy of the parameter
     }
     for (;;) {
         __syncthreads();
@@ -388,8 +495,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSm) k_tile_push_re
         __syncthreads();
         const int tile = tile_id;
         if (tile < 0) return;
-        if (SINGLE) tile_visit<TX, TY, TZ, SOFT>(g0, b, tile, tile - tile_base0, L, local_sweeps, S, SS);
-        else tile_visit<TX, TY, TZ, SOFT>(sg, b, tile, local_tile, L, local_sweeps, S, SS);
+        const bool ok = tile_visit<TX, TY, TZ, SOFT>(sg, b, tile, SINGLE ? tile - tile_base0 : local_tile, L,
+                                                      local_sweeps, S, SS, nbmask, &bar, phase);
+        if (!ok) return;
     }
 }
 
@@ -405,6 +513,52 @@ int sm_count() {
 
 }  // namespace
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver
+// library); null when the driver does not provide it.
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+    static const EncodeTiled fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+bool encode_tile_maps(const Grid &g, int shape, void *out) {
+    if (shape < 0 || shape >= kTileShapes) shape = 0;
+    const EncodeTiled fn = encode_fn();
+    if (!fn || g.Z % 4 != 0) return false;  // row strides must be multiples of 16 bytes
+    const int *sh = kShapes[shape];
+    const int32_t *arrays[kTileArrays] = {g.lab,   g.exc,   g.snk,   g.fdn,   g.fh[0],
+                                          g.fh[1], g.fh[2], g.fh[3], g.gs[0], g.gs[1]};
+    const int narr = g.gs[0] ? kTileArrays : kTileArrays - 2;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.Z, (cuuint64_t)g.Y, (cuuint64_t)g.X};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.Z * 4, (cuuint64_t)g.Y * g.Z * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)sh[2], (cuuint32_t)sh[1], (cuuint32_t)sh[0]};
+    const cuuint32_t unit[3] = {1, 1, 1};
+    static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+    for (int a = 0; a < narr; ++a) {
+        if (reinterpret_cast<uintptr_t>(arrays[a]) % 16 != 0) return false;
+        CUtensorMap m;
+        if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, const_cast<int32_t *>(arrays[a]), dims, strides, box, unit,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        std::memcpy(static_cast<char *>(out) + a * kTensorMapBytes, &m, kTensorMapBytes);
+    }
+    return true;
+}
+
 long long tile_count(const Grid &g, int shape) {
     const TileGeom t = geom(g, shape < 0 || shape >= kTileShapes ? 0 : shape);
     return (long long)t.ntx * t.nty * t.ntz;
@@ -419,7 +573,7 @@ long long tile_count_max(const Grid &g) {
 template <int TX, int TY, int TZ, bool SOFT, bool SINGLE>
 cudaError_t launch_tile_instance(const Batch &b, const Grid &g0, int tile_base0, const TileLists &L, int local_sweeps,
                                  int blocks, cudaStream_t st) {
-    const size_t smem = sizeof(TileSmem) + (SOFT ? sizeof(TileSoft) : 0);
+    const size_t smem = sizeof(TileSmem) + (SOFT ? sizeof(TileSoft) : 0) + 128;  // + alignment slack
     static bool configured = false;
     if (!configured) {
         const cudaError_t e = cudaFuncSetAttribute(k_tile_push_relabel<TX, TY, TZ, SOFT, SINGLE>,

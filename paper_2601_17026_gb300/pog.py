@@ -28,6 +28,7 @@ POG_FLAG_NO_GAP = 1
 POG_FLAG_TIMING = 2
 POG_FLAG_NO_PREPUSH = 4
 POG_FLAG_NODE_SWEEPS = 8
+POG_FLAG_NO_TMA = 16
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
@@ -346,7 +347,13 @@ def pog_solve_noalloc(cost, delta: int, alpha: int, heights, options: pog_option
     `heights` is a caller-owned int32 CUDA tensor [X, Y]. Returns the flow value."""
     import torch
 
+    if not isinstance(cost, torch.Tensor) or cost.dim() != 3:
+        raise PogError(POG_E_INVALID, "cost must be a CUDA tensor [X, Y, Z]")
     X, Y, Z = cost.shape
+    # the library writes X*Y heights through this pointer and cannot check its size
+    if (not isinstance(heights, torch.Tensor) or tuple(heights.shape) != (X, Y)
+            or heights.device != cost.device):
+        raise PogError(POG_E_INVALID, "heights must be an int32 tensor [X, Y] on the device of cost")
     flow = ctypes.c_int64(0)
     _check(load().pog_solve_noalloc(_dev(cost, torch.int32, "cost"), X, Y, Z, int(delta), int(alpha),
                                     ctypes.byref(options) if options else None, _stream(stream), ctypes.byref(flow),

@@ -261,3 +261,10 @@ def diff_volumes_f32(seed: int = BASE_SEED, count: int = 16, size: int = 128) ->
 
 DIFF_DELTA = 2
 DIFF_ALPHA = 10.0  # soft penalty of the differentiable workload, in float cost units
+DIFF_MARGIN = 1.0  # structured-hinge margin per mismatched column, in float cost units
+
+
+def diff_target(count: int = 16, size: int = 128) -> np.ndarray:
+    """int32 [B, S, S]: the hinge target surface of the differentiable workload, flat at
+    height S/2 in every column (feasible for any delta)."""
+    return np.full((count, size, size), size // 2, dtype=np.int32)

@@ -3,6 +3,7 @@
     python tests/golden/make_golden.py small      # seconds
     python tests/golden/make_golden.py medium     # about an hour on one core
     python tests/golden/make_golden.py batch [K]  # the first K volumes of the uneven batch
+    python tests/golden/make_golden.py diff [W]   # the 16 float volumes of 128^3, W threads
 
 Each file records the workload, the oracle's max-flow value and its surface (in full for
 the small volume; as a SHA-256 of the int32 heights plus their sum otherwise). Nothing
@@ -36,6 +37,35 @@ def record(vol, full_heights=False):
     return out
 
 
+def record_diff(args):
+    """One volume of the differentiable workload: the energy solve and the loss-augmented
+    solve of the structured hinge, on the quantised costs round_half_even(1024 * c)."""
+    b, fc, ht = args
+    t = time.time()
+    scale, aq, mq = 1024.0, int(synth.DIFF_ALPHA * 1024), int(synth.DIFF_MARGIN * 1024)
+    cq = np.rint(fc.astype(np.float64) * scale).astype(np.int32)  # exact: x1024 is exact in fp32
+    X, Y, Z = cq.shape
+    ref = oracle.solve(cq, synth.DIFF_DELTA, aq)
+    e, ok = oracle.energy(cq, ref.heights, synth.DIFF_DELTA, aq)
+    assert ok
+    aug = cq.copy()
+    idx = ht[:, :, None]
+    np.put_along_axis(aug, idx, np.take_along_axis(cq, idx, 2) + mq, axis=2)
+    ra = oracle.solve(aug, synth.DIFF_DELTA, aq)
+    ea, ok = oracle.energy(aug, ra.heights, synth.DIFF_DELTA, aq)
+    assert ok
+    et, ok = oracle.energy(cq, ht, synth.DIFF_DELTA, aq)
+    assert ok
+    h = np.ascontiguousarray(ref.heights, dtype=np.int32)
+    hh = np.ascontiguousarray(ra.heights, dtype=np.int32)
+    return {"volume": b, "shape": [X, Y, Z], "delta": synth.DIFF_DELTA, "alpha_q": aq, "margin_q": mq,
+            "flow": ref.flow, "energy": e, "heights_sha256": hashlib.sha256(h.tobytes()).hexdigest(),
+            "heights_sum": int(h.sum()), "aug_flow": ra.flow, "aug_energy": ea,
+            "aug_heights_sha256": hashlib.sha256(hh.tobytes()).hexdigest(), "aug_heights_sum": int(hh.sum()),
+            "target_energy": et, "hinge_q": et - (ea - mq * X * Y),
+            "oracle_seconds": round(time.time() - t, 1)}
+
+
 def main():
     which = sys.argv[1] if len(sys.argv) > 1 else "small"
     if which == "small":
@@ -50,6 +80,18 @@ def main():
         vols = synth.batch_volumes(limit=k)
         with ThreadPoolExecutor(workers) as ex:  # the oracle releases the GIL inside C
             data = {"volumes": list(ex.map(record, vols))}
+    elif which == "diff":
+        from concurrent.futures import ThreadPoolExecutor
+
+        workers = int(sys.argv[2]) if len(sys.argv) > 2 else 1
+        fc = synth.diff_volumes_f32()
+        ht = synth.diff_target()
+        with ThreadPoolExecutor(workers) as ex:
+            vols = list(ex.map(record_diff, [(b, fc[b], ht[b]) for b in range(fc.shape[0])]))
+        data = {"workload": "16 float32 volumes of 128^3, N(0,1) + horizon pattern, quantised by 1024; "
+                            "hinge target flat at height 64, margin 1024",
+                "oracle": "explicit-edge Dinic (oracle/pog_oracle.c)",
+                "generator": f"paper_2601_17026_gb300.synth, seed {synth.BASE_SEED}", "volumes": vols}
     else:
         raise SystemExit(f"unknown set {which}")
     path = os.path.join(HERE, f"{which}.json")
