@@ -68,6 +68,12 @@ typedef struct {
     int32_t tile_shape;         /* 0: 4x8 columns x 32 heights, 1: 8x8x16, 2: 4x4x64, 3: 2x4x128 */
     int32_t bfs_bottom_up_ratio; /* BFS level runs bottom-up when frontier * ratio > unlabelled
                                     nodes; 0 = default (8), < 0 = always top-down */
+    /* Test hooks for the failure paths (leave 0 in production): */
+    int32_t test_wait_limit;    /* polls of the searches' grid-barrier wait before it gives up and
+                                   the call returns POG_E_TIMEOUT; 0 = the built-in limit */
+    int32_t test_fail_alloc;    /* k > 0: the k-th allocation of a graph build (1 device state,
+                                   2 tensor-map table, 3 pinned counters) fails as if memory had
+                                   run out (POG_E_NOMEM, nothing kept) */
 } pog_options;
 
 #define POG_FLAG_NO_GAP 1     /* disable the gap heuristic between global relabels */
@@ -75,6 +81,8 @@ typedef struct {
 #define POG_FLAG_NO_PREPUSH 4 /* skip the column pre-push along the down arcs */
 #define POG_FLAG_NODE_SWEEPS 8 /* node-parallel sweeps instead of shared-memory tiles */
 #define POG_FLAG_NO_TMA 16    /* load shared-memory tiles word by word, not by bulk tensor copies */
+#define POG_FLAG_COLD_HINGE 32 /* pog_solve_batch_f32_hinge: solve the loss-augmented problem from
+                                  scratch instead of from the energy solve's final state */
 
 /* Counters of the last pog_maxflow. */
 typedef struct {
@@ -265,6 +273,37 @@ POG_API pog_status pog_solve_batch_f32(int32_t B, const float *cost_dev, float s
                                        int32_t margin, int32_t X, int32_t Y, int32_t Z, int32_t delta,
                                        int32_t alpha, const pog_options *opt, void *stream, int64_t *flows_out,
                                        int64_t *energies_out, int32_t *heights_dev);
+
+/*
+ * Structured-hinge forward of B float32 volumes of one shape in one call: the energy
+ * solve, the loss-augmented solve and the loss (the differentiable path). Each volume is
+ * quantised to cq = round_half_even(scale * c) as in pog_solve_batch_f32, then
+ *   E*     = min_h E(h) (Eq. 1 on cq), with its minimal surface h*;
+ *   E'*    = min_h E'(h), E' the energy of the costs with `margin` added at node
+ *            (x, y, h_t(x, y)) of every column, with its minimal surface h_hat; so
+ *            min_h [E(h) - margin * Hamming(h, h_t)] = E'* - margin * X * Y;
+ *   L      = E(h_t) - (E'* - margin * X * Y), the structured hinge loss (>= 0 when h_t is
+ *            feasible), whose subgradient in the costs is onehot(h_t) - onehot(h_hat).
+ * The loss-augmented problem is solved from the final residual state of the energy solve
+ * (its costs differ at one node per column, and the state becomes a preflow of it by
+ * raising two terminal capacities per column), unless POG_FLAG_COLD_HINGE is set.
+ *   cost_dev       : device float32 [B][X][Y][Z].
+ *   h_target_dev   : device int32 [B][X][Y], heights in [0, Z) (else POG_E_INVALID).
+ *   margin         : 0 <= margin < 2^28, in quantised units.
+ *   energies_out   : host int64 [B], E*.
+ *   aug_energies_out : host int64 [B] or NULL, E'*.
+ *   hinge_out      : host int64 [B], L in quantised units.
+ *   flows_out, aug_flows_out : host int64 [B] or NULL, the max-flow values of the two
+ *                    problems' graphs (Section 1.2 construction).
+ *   heights_dev, h_hat_dev : device int32 [B][X][Y], h* and h_hat.
+ * Blocks until done.
+ */
+POG_API pog_status pog_solve_batch_f32_hinge(int32_t B, const float *cost_dev, float scale,
+                                             const int32_t *h_target_dev, int32_t margin, int32_t X, int32_t Y,
+                                             int32_t Z, int32_t delta, int32_t alpha, const pog_options *opt,
+                                             void *stream, int64_t *energies_out, int64_t *aug_energies_out,
+                                             int64_t *hinge_out, int64_t *flows_out, int64_t *aug_flows_out,
+                                             int32_t *heights_dev, int32_t *h_hat_dev);
 
 /*
  * Solve one volume without allocating anything (the paper has no counterpart; this

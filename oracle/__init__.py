@@ -60,6 +60,9 @@ def _configure(lib):
     lib.oracle_cut_capacity.restype = ctypes.c_int64
     lib.oracle_cut_capacity.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int64, i32p]
+    lib.oracle_solve_state.restype = ctypes.c_int
+    lib.oracle_solve_state.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int64, i64p, i32p] + [i32p] * 6
     lib.oracle_certify.restype = ctypes.c_int
     lib.oracle_certify.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_int64] + [i32p] * 7 + [ctypes.c_int64]
@@ -117,6 +120,28 @@ def solve(cost, delta: int, alpha: int, check: bool = False, lib=None) -> Oracle
     if rc != 0:
         raise RuntimeError(f"oracle_solve failed: {ERRORS.get(rc, rc)}")
     return OracleResult(int(flow.value), heights, *[int(v) for v in stats])
+
+
+def solve_state(cost, delta: int, alpha: int, lib=None):
+    """(flow, heights, state): the oracle's max flow described in the layout of a solver's
+    exported state (the dict ``certify`` takes: excess, sink, fdown, fhard, gsoft, in_cut;
+    the bottom layer counted as part of the source), for checking the certificate on a
+    state known to be optimal."""
+    lib = lib or _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    N = X * Y * Z
+    heights = np.empty((X, Y), dtype=np.int32)
+    st = {k: np.empty(N, dtype=np.int32) for k in ("excess", "sink", "fdown", "in_cut")}
+    st["fhard"] = np.empty(4 * N, dtype=np.int32)
+    st["gsoft"] = np.empty(2 * N, dtype=np.int32)
+    flow = ctypes.c_int64(0)
+    rc = lib.oracle_solve_state(_i32(c), X, Y, Z, int(delta), int(alpha), ctypes.byref(flow), _i32(heights),
+                                _i32(st["excess"]), _i32(st["sink"]), _i32(st["fdown"]), _i32(st["fhard"]),
+                                _i32(st["gsoft"]), _i32(st["in_cut"]))
+    if rc != 0:
+        raise RuntimeError(f"oracle_solve_state failed: {ERRORS.get(rc, rc)}")
+    return int(flow.value), heights, st
 
 
 def energy(cost, heights, delta: int, alpha: int):

@@ -326,6 +326,115 @@ done:
 }
 
 /*
+ * Solve one volume as oracle_solve does and describe the final flow in the layout of a
+ * solver state (the arrays oracle_certify takes, include/pog.h's export), so that the
+ * certificate can be checked on a state known to be optimal. The literal graph keeps the
+ * bottom layer z = 0 as nodes; the exported state treats it as part of the source, so
+ * for every node v above it:
+ *   sink   = residual capacity of v -> t,
+ *   excess = unused capacity of s -> v (the state has every source arc saturated) plus
+ *            the flow v sends into bottom-layer nodes (arcs that the state does not keep),
+ *   fdown  = flow on v -> (x,y,z-1) for z >= 2, fhard[d] = flow on the hard arc towards
+ *            neighbour d when it lands at z - delta >= 1, gsoft[k] = flow v -> q minus
+ *            flow q -> v for the neighbour q at x+1 (k = 0) or y+1 (k = 1),
+ *   in_cut = 1 for the nodes reachable from s in the final residual graph.
+ * Arcs are told apart by their heads and initial capacities (infinite or alpha).
+ */
+int oracle_solve_state(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta, int64_t alpha,
+                       int64_t *flow_out, int32_t *heights_out, int32_t *excess, int32_t *sink, int32_t *fdown,
+                       int32_t *fhard, int32_t *gsoft, int32_t *in_cut) {
+    if (!cost || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 || !flow_out || !heights_out || !excess ||
+        !sink || !fdown || !fhard || !gsoft || !in_cut)
+        return ORC_E_ARGS;
+    if ((int64_t)X * Y * Z + 2 > INT32_MAX) return ORC_E_ARGS;
+    orc_graph g;
+    int rc = graph_build(&g, cost, X, Y, Z, delta, alpha, 1);
+    if (rc != ORC_OK) return rc;
+    const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
+    orc_dinic d = {0};
+    d.level = malloc((size_t)g.n * sizeof(int32_t));
+    d.queue = malloc((size_t)g.n * sizeof(int64_t));
+    d.iter = malloc((size_t)g.n * sizeof(int64_t));
+    d.path = malloc((size_t)g.n * sizeof(int64_t));
+    uint8_t *in_s = malloc((size_t)g.n);
+    int64_t *acc = calloc((size_t)N * 9, sizeof(int64_t)); /* excess, fdown, fhard[4], gsoft[2], sink */
+    if (!d.level || !d.queue || !d.iter || !d.path || !in_s || !acc) {
+        rc = ORC_E_NOMEM;
+        goto done;
+    }
+    int64_t flow = 0;
+    while (dinic_bfs(&g, &d, s, t)) flow += dinic_blocking_flow(&g, &d, s, t);
+    residual_reach(&g, s, in_s, d.queue);
+    int64_t *exc = acc, *fdn = acc + N, *fh = acc + 2 * N, *gs = acc + 6 * N, *snk = acc + 8 * N;
+    /* source arcs: the unused capacity stays at the node as excess */
+    for (int64_t a = g.first[s]; a < g.first[s + 1]; ++a) {
+        const int64_t v = g.head[a];
+        if (g.cap0[a] > 0 && v % Z != 0) exc[v] += g.cap[a];
+    }
+    for (int64_t u = 0; u < N; ++u) {
+        const int64_t z = u % Z, col = u / Z, x = col / Y, y = col % Y;
+        if (z == 0) continue;
+        for (int64_t a = g.first[u]; a < g.first[u + 1]; ++a) {
+            if (g.cap0[a] <= 0) continue; /* a reverse half-arc */
+            const int64_t h = g.head[a], f = g.cap0[a] - g.cap[a];
+            if (h == t) {
+                snk[u] = g.cap[a];
+                continue;
+            }
+            const int64_t hz = h % Z, hcol = h / Z, hx = hcol / Y, hy = hcol % Y;
+            if (hz == 0) { /* into the bottom layer: not an arc of the state */
+                exc[u] += f;
+                continue;
+            }
+            if (hcol == col) { /* the column arc (x,y,z) -> (x,y,z-1) */
+                fdn[u] += f;
+                continue;
+            }
+            int dir = -1;
+            for (int k = 0; k < 4; ++k)
+                if (hx == x + DX[k] && hy == y + DY[k]) dir = k;
+            if (dir < 0) {
+                rc = ORC_E_ARGS;
+                goto done;
+            }
+            if (g.cap0[a] == ORC_INF) { /* hard arc landing at z - delta >= 1 */
+                fh[dir * N + u] += f;
+            } else if (dir & 1) { /* soft arc towards x+1 / y+1 */
+                gs[(dir >> 1) * N + u] += f;
+            } else { /* soft arc towards x-1 / y-1: counts against the neighbour's pair */
+                gs[(dir >> 1) * N + h] -= f;
+            }
+        }
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        const int bottom = v % Z == 0;
+        excess[v] = bottom ? 0 : (int32_t)exc[v];
+        sink[v] = bottom ? 0 : (int32_t)snk[v];
+        fdown[v] = bottom ? 0 : (int32_t)fdn[v];
+        for (int k = 0; k < 4; ++k) fhard[k * N + v] = bottom ? 0 : (int32_t)fh[k * N + v];
+        for (int k = 0; k < 2; ++k) gsoft[k * N + v] = bottom ? 0 : (int32_t)gs[k * N + v];
+        in_cut[v] = in_s[v];
+    }
+    for (int64_t col = 0; col < (int64_t)X * Y; ++col) {
+        int32_t hgt = -1;
+        for (int64_t z = 0; z < Z; ++z)
+            if (in_s[col * Z + z]) hgt = (int32_t)z;
+        heights_out[col] = hgt;
+        if (hgt < 0) rc = ORC_E_SURFACE;
+    }
+    *flow_out = flow;
+done:
+    free(d.level);
+    free(d.queue);
+    free(d.iter);
+    free(d.path);
+    free(in_s);
+    free(acc);
+    graph_free(&g);
+    return rc;
+}
+
+/*
  * Surface energy of Eq. 1 for a height map: E = sum_col c(col, h(col)) +
  * alpha * sum over unordered 4-neighbour pairs |h_p - h_q|. *feasible is set to 0 if
  * some pair differs by more than delta or a height is outside [0, Z).

@@ -7,7 +7,8 @@ structured-hinge loss L = E(h_t) - min_h [E(h) - margin * Hamming(h, h_t)].
 
 Backward (Danskin's theorem; E* is a minimum of functions linear in c): dE*/dc is the
 one-hot of the optimal surface, dL/dc = onehot(h_t) - onehot(h_hat) where h_hat solves
-the loss-augmented problem. Quantisation is treated as the identity in the backward
+the loss-augmented problem. The energy solve, the loss-augmented solve (started from the
+energy solve's final state) and the loss value are one library call. Quantisation is treated as the identity in the backward
 (the exact gradient of the quantised problem, scaled back to float units). One backward
 kernel writes the whole gradient volume.
 """
@@ -47,16 +48,17 @@ class PogSolve(torch.autograd.Function):
         cost = cost.contiguous()
         B, X, Y, Z = cost.shape
         aq = _alpha_q(alpha, scale)
-        heights, eq = _solve_all(cost, delta, aq, scale, options)
-        energy = eq.to(torch.float64) / scale
         loss = h_hat = None
-        if h_target is not None:
+        if h_target is None:
+            heights, eq = _solve_all(cost, delta, aq, scale, options)
+        else:
+            # energy solve, loss-augmented solve (warm-started) and the hinge value, in one call
             h_target = h_target.to(device=cost.device, dtype=torch.int32).contiguous()
-            mq = _alpha_q(margin, scale)
-            h_hat, eaug = _solve_all(cost, delta, aq, scale, options, h_aug=h_target, margin_q=mq)
-            et = pog.pog_surface_energy(cost, scale, h_target, aq).cpu()
-            # min_h [E(h) - m * Hamming] = E'*(h_hat) - m * X * Y, with E' the augmented energy
-            loss = (et - (eaug - mq * X * Y)).to(torch.float64) / scale
+            r = pog.pog_solve_batch_f32_hinge(cost, scale, h_target, _alpha_q(margin, scale), delta, aq, options)
+            heights, h_hat = r["heights"], r["h_hat"]
+            eq = torch.tensor(r["energies"], dtype=torch.int64)
+            loss = torch.tensor(r["hinge"], dtype=torch.int64).to(torch.float64) / scale
+        energy = eq.to(torch.float64) / scale
         ctx.save_for_backward(heights, h_target, h_hat)
         ctx.mark_non_differentiable(heights)
         if h_hat is not None:

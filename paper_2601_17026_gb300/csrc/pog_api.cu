@@ -55,6 +55,8 @@ void set_options(pog_graph *g, const pog_options *opt) {
     g->tile_shape = (opt && opt->tile_shape > 0 && opt->tile_shape < pog::kTileShapes) ? opt->tile_shape : 0;
     g->bu_ratio = !opt || opt->bfs_bottom_up_ratio == 0 ? kBottomUpRatio
                                                          : (opt->bfs_bottom_up_ratio < 0 ? 0 : opt->bfs_bottom_up_ratio);
+    g->wait_limit = (opt && opt->test_wait_limit > 0) ? opt->test_wait_limit : 0;
+    g->fail_alloc = (opt && opt->test_fail_alloc > 0) ? opt->test_fail_alloc : 0;
 }
 
 template <class T>
@@ -359,19 +361,21 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     const size_t table = 2 * (align_up(sizeof(Grid) * n, 256) + 2 * align_up(sizeof(int) * (n + 1), 256));
     g->arena_bytes = per * (8 + 2) + 2 * per_soft + heights + ctr + vctr + sync + trace + 4 * tile_bytes + 256 + table +
                      visit + tmaps;
-    cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
+    cudaError_t e = g->fail_alloc == 1 ? cudaErrorMemoryAllocation : cudaMalloc(&g->arena, g->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g->arena = nullptr;
         pog_free(g);
         return e == cudaErrorMemoryAllocation ? POG_E_NOMEM : POG_E_CUDA;
     }
-    g->tmap_host = std::calloc((size_t)n * pog::kTileArrays, pog::kTensorMapBytes);
+    g->tmap_host = g->fail_alloc == 2 ? nullptr : std::calloc((size_t)n * pog::kTileArrays, pog::kTensorMapBytes);
     if (!g->tmap_host) {
         pog_free(g);
         return POG_E_NOMEM;
     }
-    e = cudaHostAlloc(reinterpret_cast<void **>(&g->ctr_host), sizeof(DevCounters) * (n + 1), cudaHostAllocDefault);
+    e = g->fail_alloc == 3 ? cudaErrorMemoryAllocation
+                           : cudaHostAlloc(reinterpret_cast<void **>(&g->ctr_host), sizeof(DevCounters) * (n + 1),
+                                           cudaHostAllocDefault);
     if (e != cudaSuccess) {
         g->ctr_host = nullptr;
         pog_free(g);
@@ -448,6 +452,7 @@ pog_status build_batch(int n, const VolumeSpec *spec, const pog_options *opt, vo
     g->batch.ctr = g->ctr;
     g->batch.trace = g->trace;
     g->batch.visit = g->visit;
+    g->batch.wait_limit = g->wait_limit;
     e = cudaMemcpyAsync(g->tmap_dev, g->tmap_host, (size_t)n * pog::kTileArrays * pog::kTensorMapBytes,
                         cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->vols_dev, g->vols, sizeof(Grid) * n, cudaMemcpyHostToDevice, g->stream);
@@ -739,6 +744,84 @@ pog_status pog_solve_batch_f32(int32_t B, const float *cost_dev, float scale, co
         s = from_cuda(cudaMemcpyAsync(heights_dev, g->heights, sizeof(int32_t) * cols * B, cudaMemcpyDeviceToDevice,
                                       g->stream));
     }
+    pog_free(g);  // synchronises the stream first
+    return s;
+}
+
+pog_status pog_solve_batch_f32_hinge(int32_t B, const float *cost_dev, float scale, const int32_t *h_target_dev,
+                                     int32_t margin, int32_t X, int32_t Y, int32_t Z, int32_t delta, int32_t alpha,
+                                     const pog_options *opt, void *stream, int64_t *energies_out,
+                                     int64_t *aug_energies_out, int64_t *hinge_out, int64_t *flows_out,
+                                     int64_t *aug_flows_out, int32_t *heights_dev, int32_t *h_hat_dev) {
+    if (B < 0 || !(scale > 0.0f) || margin < 0 || margin >= (1 << 28)) return POG_E_INVALID;
+    if (B > 0 && (!cost_dev || !h_target_dev || !energies_out || !hinge_out || !heights_dev || !h_hat_dev))
+        return POG_E_INVALID;
+    if (B == 0) return POG_OK;
+    if (B > pog::kMaxVolumes) return POG_E_INVALID;
+    VolumeSpec *spec = new (std::nothrow) VolumeSpec[B];
+    if (!spec) return POG_E_NOMEM;
+    for (int i = 0; i < B; ++i) spec[i] = VolumeSpec{X, Y, Z, delta, alpha};
+    const size_t vol = (size_t)X * Y * Z, cols = (size_t)X * Y;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pog_graph *g = nullptr;
+    pog_status s = build_batch(B, spec, opt, stream, &g, [&](int v, const Grid &gr, cudaStream_t q) {
+        return pog::launch_build_f32(gr, cost_dev + v * vol, scale, nullptr, 0, q);
+    });
+    if (s != POG_OK) {
+        delete[] spec;
+        return s;
+    }
+    long long *et = reinterpret_cast<long long *>(std::malloc(sizeof(long long) * B));
+    if (!et) s = POG_E_NOMEM;
+    // E(h_t) of every target on the quantised costs, first: a height outside [0, Z) is an
+    // invalid argument. The relabel queue serves as scratch (the solves overwrite it later).
+    if (s == POG_OK)
+        s = from_cuda(pog::launch_surface_energy(cost_dev, scale, h_target_dev, B, X, Y, Z, alpha,
+                                                 reinterpret_cast<long long *>(g->queue_a), st));
+    if (s == POG_OK)
+        s = from_cuda(cudaMemcpyAsync(et, g->queue_a, sizeof(long long) * B, cudaMemcpyDeviceToHost, st));
+    if (s == POG_OK) s = from_cuda(cudaStreamSynchronize(st));
+    for (int i = 0; s == POG_OK && i < B; ++i)
+        if (et[i] == (long long)0x8000000000000000ull) s = POG_E_INVALID;
+    // the energy solve
+    if (s == POG_OK) s = maxflow_impl(g);
+    if (s == POG_OK) {
+        for (int i = 0; i < B; ++i) {
+            const DevCounters &c = volume_counters(g, i);
+            const long long K = -1 - (long long)c.bottom_sum + (long long)c.src_total + (long long)c.neg_bottom;
+            energies_out[i] = g->flows[i] - K;
+            if (flows_out) flows_out[i] = g->flows[i];
+        }
+        s = from_cuda(cudaMemcpyAsync(heights_dev, g->heights, sizeof(int32_t) * cols * B, cudaMemcpyDeviceToDevice, st));
+    }
+    // the loss-augmented solve: from the energy solve's final state (warm), or rebuilt
+    const bool cold = opt && (opt->flags & POG_FLAG_COLD_HINGE);
+    if (s == POG_OK && cold) {
+        pog_free(g);
+        g = nullptr;
+        s = build_batch(B, spec, opt, stream, &g, [&](int v, const Grid &gr, cudaStream_t q) {
+            return pog::launch_build_f32(gr, cost_dev + v * vol, scale, h_target_dev + v * cols, margin, q);
+        });
+    } else if (s == POG_OK) {
+        for (int v = 0; v < B && s == POG_OK; ++v)
+            s = from_cuda(pog::launch_augment(g->vols[v], cost_dev + v * vol, scale, h_target_dev + v * cols, margin,
+                                              st));
+    }
+    if (s == POG_OK) s = maxflow_impl(g);
+    if (s == POG_OK) {
+        for (int i = 0; i < B; ++i) {
+            const DevCounters &c = volume_counters(g, i);
+            const long long K = -1 - (long long)c.bottom_sum + (long long)c.src_total + (long long)c.neg_bottom;
+            const long long eaug = g->flows[i] - K;  // E'(h_hat), the augmented energy
+            if (aug_energies_out) aug_energies_out[i] = eaug;
+            if (aug_flows_out) aug_flows_out[i] = g->flows[i] - (cold ? 0 : (long long)c.aug_offset);
+            // min_h [E(h) - margin * Hamming(h, h_t)] = E'(h_hat) - margin * X * Y
+            hinge_out[i] = et[i] - (eaug - (long long)margin * (long long)cols);
+        }
+        s = from_cuda(cudaMemcpyAsync(h_hat_dev, g->heights, sizeof(int32_t) * cols * B, cudaMemcpyDeviceToDevice, st));
+    }
+    delete[] spec;
+    std::free(et);
     pog_free(g);  // synchronises the stream first
     return s;
 }

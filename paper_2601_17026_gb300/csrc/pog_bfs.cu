@@ -32,7 +32,7 @@ constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1-2 s of polling at wors
 // each launch): the k-th barrier is passed once the counter reaches k * nblocks. One
 // atomic per block and a polling load, no second word to flip. False once the wait
 // timed out (POG_ERR_TIMEOUT is raised and every block leaves).
-__device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err) {
+__device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err, int limit) {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
@@ -40,9 +40,10 @@ __device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err
         __threadfence();  // this block's writes before its arrival
         const unsigned old = atomicAdd(&s->count, 1u);
         const unsigned target = (old / nblocks + 1) * nblocks;
+        const long long spin_limit = limit > 0 ? limit : kBarrierSpinLimit;
         long long spins = 0;
         while ((int)(*(volatile unsigned *)&s->count - target) < 0) {
-            if (++spins > kBarrierSpinLimit || (*(volatile int *)err & POG_ERR_TIMEOUT)) {
+            if (++spins > spin_limit || (*(volatile int *)err & POG_ERR_TIMEOUT)) {
                 atomicOr(err, POG_ERR_TIMEOUT);
                 ok = 0;
                 break;
@@ -98,15 +99,16 @@ __device__ __forceinline__ void decode(const Grid &g, int u, int &x, int &y, int
 template <bool RO>
 __device__ __forceinline__ void gather_in_any(const Grid &g, int v, int x, int y, int z, Hood &h,
                                               const unsigned *visit, int base) {
-    if (g.gs[0]) gather_in<true, RO>(g, v, x, y, z, h, visit, base);
-    else gather_in<false, RO>(g, v, x, y, z, h, visit, base);
+    if (g.gs[0]) gather_in<true, RO, true>(g, v, x, y, z, h, visit, base);
+    else gather_in<false, RO, true>(g, v, x, y, z, h, visit, base);
 }
 
+// Out-arcs of u with their residuals (infinite arcs taken as residual without a load).
 template <bool RO>
 __device__ __forceinline__ void gather_out_any(const Grid &g, int u, int x, int y, int z, Hood &h,
                                                const int32_t *far = nullptr) {
-    if (g.gs[0]) gather_out<true, RO>(g, u, x, y, z, h, far);
-    else gather_out<false, RO>(g, u, x, y, z, h, far);
+    if (g.gs[0]) gather_out<true, RO, true>(g, u, x, y, z, h, far);
+    else gather_out<false, RO, true>(g, u, x, y, z, h, far);
 }
 
 // Bottom-up test of an unlabelled node u: does one of its residual out-arcs end at a
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ones += __shfl_down_sync(0xffffffffu, ones, o);
     if ((threadIdx.x & 31) == 0 && ones) atomicAdd(&s->level1, ones);
-    if (!grid_sync(s, nblocks, err)) return;
+    if (!grid_sync(s, nblocks, err, b.wait_limit)) return;
     unvisited -= *(volatile int *)&s->level1;
     if (tid == 0 && b.trace) b.trace[0] = LevelTrace{*(volatile int *)&s->level1, 2, (long long)t_start, 0};
     int level = 2;
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
                 warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
             }
         }
-        if (!grid_sync(s, nblocks, err)) return;
+        if (!grid_sync(s, nblocks, err, b.wait_limit)) return;
         int *t = cur;
         cur = nxt;
         nxt = t;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_cut_reach(
             if (seed) warp_append(base + u, qa, &s->size[1]);
         }
     }
-    if (!grid_sync(s, nblocks, err)) return;
+    if (!grid_sync(s, nblocks, err, b.wait_limit)) return;
     int level = 1;
     int *cur = qa, *nxt = qb;
     __shared__ int frontier;
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_cut_reach(
             }
             warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
         }
-        if (!grid_sync(s, nblocks, err)) return;
+        if (!grid_sync(s, nblocks, err, b.wait_limit)) return;
         int *t = cur;
         cur = nxt;
         nxt = t;

@@ -41,6 +41,7 @@ struct DevCounters {
     unsigned long long active;       // active nodes (excess > 0, label < INF)
     unsigned long long raised;       // labels raised by the last gap relabel
     unsigned long long tiles_visited;  // tile visits of the tiled sweeps
+    unsigned long long aug_offset;   // warm loss augmentation: what every cut gained (see k_augment)
     int changed;                     // a relaxation pass changed something
     int error;                       // POG_ERR_* bits
     int gap_level;                   // first empty label level found, or 0
@@ -105,6 +106,7 @@ struct Batch {
     DevCounters *ctr;      // union counters: active nodes, BFS levels, gap, tile visits, timeouts
     LevelTrace *trace;     // per-level trace of the last global relabel (may be null)
     unsigned *visit;       // global relabel: one bit per union node, set once it is labelled
+    int wait_limit;        // polls of a grid-barrier wait before it gives up (0: built-in limit)
 };
 
 // Largest v with base[v] <= idx (base ascending, base[0] = 0, nvol entries searched).
@@ -150,9 +152,15 @@ __device__ __forceinline__ int ld_arc(const int32_t *p) {
     return RO ? __ldg(p) : __ldcg(p);
 }
 
+// Infinite arcs: their forward residual is POG_CAP_INF minus their flow, and no flow
+// reaches POG_CAP_INF without the solve failing with POG_E_OVERFLOW (every push checks),
+// so in a search whose result is used they are always residual. INF_RES takes them so
+// without loading their flow words (the searches that only need to know whether an arc
+// is residual); the pushes, which need the amount, load it.
+
 // Out-arcs of u: slot 0 down, 1 up, 2+3d hard out, 3+3d hard in (reverse), 4+3d soft.
 // `far` (default: the labels) is the array read at each far end into h.lab.
-template <bool SOFT, bool RO = false>
+template <bool SOFT, bool RO = false, bool INF_RES = false>
 __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, int z, Hood &h,
                                            const int32_t *far = nullptr) {
 #pragma unroll
@@ -162,7 +170,7 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
     }
     if (z >= 2) {
         h.node[0] = u - 1;
-        h.res[0] = POG_CAP_INF - ld_arc<RO>(g.fdn + u);
+        h.res[0] = INF_RES ? 1 : POG_CAP_INF - ld_arc<RO>(g.fdn + u);
     }
     if (z + 1 < g.Z) {
         h.node[1] = u + 1;
@@ -175,7 +183,7 @@ __device__ __forceinline__ void gather_out(const Grid &g, int u, int x, int y, i
         if (!ok) continue;
         if (z - g.delta >= 1) {
             h.node[2 + 3 * d] = u + off - g.delta;
-            h.res[2 + 3 * d] = POG_CAP_INF - ld_arc<RO>(g.fh[d] + u);
+            h.res[2 + 3 * d] = INF_RES ? 1 : POG_CAP_INF - ld_arc<RO>(g.fh[d] + u);
         }
         if (z + g.delta < g.Z) {
             const int v = u + off + g.delta;
@@ -236,7 +244,7 @@ __device__ __forceinline__ bool out_arc(const Grid &g, int u, int x, int y, int 
 // (q, z+D), 3+3d reverse of v's hard arc, 4+3d soft. With `visit`, h.lab receives the
 // visited-bitmap word of each tail (union node base + u) instead of its label, all bits
 // set for an absent arc.
-template <bool SOFT, bool RO = false>
+template <bool SOFT, bool RO = false, bool INF_RES = false>
 __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, int z, Hood &h,
                                           const unsigned *visit = nullptr, int base = 0) {
 #pragma unroll
@@ -246,7 +254,7 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
     }
     if (z + 1 < g.Z) {
         h.node[0] = v + 1;
-        h.res[0] = POG_CAP_INF - ld_arc<RO>(g.fdn + v + 1);
+        h.res[0] = INF_RES ? 1 : POG_CAP_INF - ld_arc<RO>(g.fdn + v + 1);
     }
     if (z >= 2) {
         h.node[1] = v - 1;
@@ -260,7 +268,7 @@ __device__ __forceinline__ void gather_in(const Grid &g, int v, int x, int y, in
         if (z + g.delta < g.Z) {
             const int u = v + off + g.delta;
             h.node[2 + 3 * d] = u;
-            h.res[2 + 3 * d] = POG_CAP_INF - ld_arc<RO>(g.fh[d ^ 1] + u);
+            h.res[2 + 3 * d] = INF_RES ? 1 : POG_CAP_INF - ld_arc<RO>(g.fh[d ^ 1] + u);
         }
         if (z - g.delta >= 1) {
             h.node[3 + 3 * d] = v + off - g.delta;
@@ -334,6 +342,7 @@ struct pog_graph {
     int sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks;
     float relabel_factor;
     int tile_shape, bu_ratio;
+    int wait_limit, fail_alloc;  // test hooks of pog_options
     cudaEvent_t round_ev[4];     // global relabel start/stop, sweep block start/stop
     long long stats[8];
     // POG_FLAG_TIMING: event pairs per kernel family, folded into ms[] after a sync

@@ -119,6 +119,74 @@ __global__ void k_bottom_const(Grid g, Cost cost) {
 }
 
 // ----------------------------------------------------------------------------------
+// Warm start of the loss-augmented problem (structured hinge): the costs change only at
+// node (x, y, t) of every column, t = h_t(x, y), by +margin. So w(t) grows by margin and
+// w(t+1) shrinks by margin, and the final residual state of the plain problem becomes a
+// valid preflow of the augmented one by two capacity increases per column: the sink arc
+// of (x, y, t) gains margin (its residual grows), and node (x, y, t+1) gains a source arc
+// of capacity margin, saturated at once (its excess grows). Its terminal capacities are
+// then cs = max(-w, 0) + margin, ct = max(w, 0) (and at t: cs = max(-w, 0), ct = max(w, 0) +
+// margin), i.e. min(cs, ct) may exceed 0; every s-t cut then has capacity larger by
+// sum min(cs, ct) than in the graph with cs = max(-w', 0), ct = max(w', 0), so the cut is
+// the same and the max-flow value of that graph is the one found minus `aug_offset`. When
+// t = 0 the bottom layer's weights change, whose constants are recomputed from the
+// augmented costs (k_bottom_sums, k_bottom_const). The source supply of the nodes above
+// the bottom layer (src_total) grows by margin per node t+1.
+// ----------------------------------------------------------------------------------
+
+// Bottom-layer sums of k_build alone (one thread per column), on possibly augmented costs.
+template <class Cost>
+__global__ void k_bottom_sums(Grid g, Cost cost) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long bsum = 0, bpos = 0, bneg = 0;
+    int err = 0;
+    if (col < g.X * g.Y) {
+        const int u = col * g.Z;
+        const int c = cost.load(u, err);
+        bsum = (unsigned long long)(long long)c;
+        if (u != 0 && c > 0) bpos = (unsigned long long)c;
+        if (u != 0 && c < 0) bneg = (unsigned long long)(-(long long)c);
+    }
+    if (err) atomicOr(&g.ctr->error, err);
+    block_add_u64(bsum, &g.ctr->bottom_sum);
+    __syncthreads();
+    block_add_u64(bpos, &g.ctr->pos_bottom);
+    __syncthreads();
+    block_add_u64(bneg, &g.ctr->neg_part);
+}
+
+// One thread per column: the capacity increases at t and t+1 (plain costs give w).
+__global__ void k_augment(Grid g, CostF32 plain, const int32_t *ht, int margin) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long supply = 0, offset = 0;
+    int err = 0;
+    if (col < g.X * g.Y) {
+        const int t = ht[col];
+        const int base = col * g.Z;
+        if (t >= 1 && t < g.Z) {
+            const int w = plain.load(base + t, err) - plain.load(base + t - 1, err);
+            const long long r = (long long)g.snk[base + t] + margin;
+            if (r > 0x7fffffffll) err |= POG_ERR_FLOW_RANGE;
+            g.snk[base + t] = (int)r;
+            if (w < 0) offset += (unsigned long long)min(-w, margin);
+        }
+        if (t >= 0 && t + 1 < g.Z) {
+            const int w = plain.load(base + t + 1, err) - plain.load(base + t, err);
+            const long long e = (long long)g.exc[base + t + 1] + margin;
+            if (e > 0x7fffffffll) err |= POG_ERR_FLOW_RANGE;
+            g.exc[base + t + 1] = (int)e;
+            supply += (unsigned long long)margin;
+            if (w > 0) offset += (unsigned long long)min(w, margin);
+        }
+        if (t < 0 || t >= g.Z) err |= POG_ERR_COST_RANGE;  // not a surface
+    }
+    if (err) atomicOr(&g.ctr->error, err);
+    block_add_u64(supply, &g.ctr->src_total);
+    __syncthreads();
+    block_add_u64(offset, &g.ctr->aug_offset);
+}
+
+// ----------------------------------------------------------------------------------
 // Column pre-push: before the first global relabel, every column pushes its excess down
 // its infinite down arcs (Section 1.2: (x,y,z) -> (x,y,z-1)), absorbing it into the sink
 // arcs it passes. Scanning from the top, the flow leaving node z downwards is
@@ -158,8 +226,10 @@ __global__ void k_column_prepush(Grid g) {
             const long long absorbed = c_in + e - c_out;  // into the sink arc
             g.snk[base + z] = (int)(sk - absorbed);
             if (z >= 2) {
-                g.fdn[base + z] = (int)c_out;
+                const long long f = (long long)g.fdn[base + z] + c_out;  // adds to any flow already there
+                g.fdn[base + z] = (int)f;
                 g.exc[base + z] = 0;
+                if (f >= 0x7fffffffll) overflow = true;
             } else {
                 g.exc[base + z] = (int)c_out;
             }
@@ -470,6 +540,21 @@ cudaError_t launch_build_f32(const Grid &g, const float *cost, float scale, cons
     CostF32 c{cost, scale, h_aug, margin, g.Z};
     k_build<<<blocks_for(g.N), kThreads, 0, st>>>(g, c);
     k_bottom_const<<<1, 1, 0, st>>>(g, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_augment(const Grid &g, const float *cost, float scale, const int32_t *ht, int margin,
+                           cudaStream_t st) {
+    // the five bottom-layer sums are consecutive counters: clear them, then recompute
+    cudaError_t e = cudaMemsetAsync(&g.ctr->bottom_sum, 0, 5 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&g.ctr->aug_offset, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    const CostF32 aug{cost, scale, ht, margin, g.Z};
+    const CostF32 plain{cost, scale, nullptr, 0, g.Z};
+    const long long cols = (long long)g.X * g.Y;
+    k_bottom_sums<<<blocks_for(cols), kThreads, 0, st>>>(g, aug);
+    k_bottom_const<<<1, 1, 0, st>>>(g, aug);
+    k_augment<<<blocks_for(cols), kThreads, 0, st>>>(g, plain, ht, margin);
     return cudaGetLastError();
 }
 

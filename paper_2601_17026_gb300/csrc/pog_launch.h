@@ -14,6 +14,10 @@ cudaError_t launch_build_i32(const Grid &g, const int32_t *cost, cudaStream_t st
 cudaError_t launch_build_f32(const Grid &g, const float *cost, float scale, const int32_t *h_aug, int margin,
                              cudaStream_t st);
 cudaError_t launch_column_prepush(const Grid &g, cudaStream_t st);
+// Turn the final state of a plain float-cost solve into a preflow of its loss-augmented
+// problem (margin added at node (x, y, ht(x, y)) of every column); see k_augment.
+cudaError_t launch_augment(const Grid &g, const float *cost, float scale, const int32_t *ht, int margin,
+                           cudaStream_t st);
 cudaError_t launch_sweep(const Batch &b, int *list, int *count, int ops, cudaStream_t st);
 cudaError_t launch_gap(const Batch &b, unsigned int *bits, int levels, cudaStream_t st);
 cudaError_t launch_heights(const Grid &g, int32_t *heights, cudaStream_t st);

@@ -144,6 +144,7 @@ extern "C" pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int3
     b.ctr = uctr;
     b.trace = nullptr;
     b.visit = visit;
+    b.wait_limit = (opt && opt->test_wait_limit > 0) ? opt->test_wait_limit : 0;
     const int bases[2] = {0, (int)N};
     const int tbases[2] = {0, (int)pog::tile_count(g, shape)};
 

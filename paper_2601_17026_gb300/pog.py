@@ -29,10 +29,12 @@ POG_FLAG_TIMING = 2
 POG_FLAG_NO_PREPUSH = 4
 POG_FLAG_NODE_SWEEPS = 8
 POG_FLAG_NO_TMA = 16
+POG_FLAG_COLD_HINGE = 32
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
-            "pog_surface_energy", "pog_solve_batch", "pog_solve_batch_f32", "pog_solve_noalloc"]
+            "pog_surface_energy", "pog_solve_batch", "pog_solve_batch_f32", "pog_solve_batch_f32_hinge",
+            "pog_solve_noalloc"]
 
 
 class PogError(RuntimeError):
@@ -45,7 +47,8 @@ class pog_options(ctypes.Structure):
     _fields_ = [("sweeps_per_relabel", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("tile_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32), ("bfs_blocks_per_sm", ctypes.c_int32),
                 ("relabel_factor", ctypes.c_float), ("tile_shape", ctypes.c_int32),
-                ("bfs_bottom_up_ratio", ctypes.c_int32)]
+                ("bfs_bottom_up_ratio", ctypes.c_int32), ("test_wait_limit", ctypes.c_int32),
+                ("test_fail_alloc", ctypes.c_int32)]
 
 
 class pog_stats_t(ctypes.Structure):
@@ -91,6 +94,8 @@ def load(path: str = LIB_PATH):
             "pog_solve_batch": [i32, ctypes.POINTER(pog_volume), opts, vp, i64p, ctypes.POINTER(vp)],
             "pog_solve_noalloc": [vp, i32, i32, i32, i32, i32, opts, vp, i64p, vp],
             "pog_solve_batch_f32": [i32, vp, f32, vp, i32, i32, i32, i32, i32, i32, opts, vp, i64p, i64p, vp],
+            "pog_solve_batch_f32_hinge": [i32, vp, f32, vp, i32, i32, i32, i32, i32, i32, opts, vp, i64p, i64p, i64p,
+                                          i64p, i64p, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -128,9 +133,10 @@ def _dev(t, dtype, name):
 
 
 def make_options(sweeps_per_relabel=0, max_rounds=0, tile_sweeps=0, flags=0, bfs_blocks_per_sm=0,
-                 relabel_factor=0.0, tile_shape=0, bfs_bottom_up_ratio=0) -> pog_options:
+                 relabel_factor=0.0, tile_shape=0, bfs_bottom_up_ratio=0, test_wait_limit=0,
+                 test_fail_alloc=0) -> pog_options:
     return pog_options(sweeps_per_relabel, max_rounds, tile_sweeps, flags, bfs_blocks_per_sm, relabel_factor,
-                       tile_shape, bfs_bottom_up_ratio)
+                       tile_shape, bfs_bottom_up_ratio, test_wait_limit, test_fail_alloc)
 
 
 def pog_strerror(status: int) -> str:
@@ -340,6 +346,34 @@ def pog_solve_batch_f32(cost, scale: float, delta: int, alpha: int, h_aug=None, 
                                       _stream(stream), flows, energies, _dev(heights, torch.int32, "heights")),
            "pog_solve_batch_f32")
     return [int(flows[i]) for i in range(B)], [int(energies[i]) for i in range(B)], heights
+
+
+def pog_solve_batch_f32_hinge(cost, scale: float, h_target, margin: int, delta: int, alpha: int,
+                              options: pog_options | None = None, stream=None) -> dict:
+    """Energy solve, loss-augmented solve and structured-hinge loss of float32 CUDA volumes
+    [B, X, Y, Z] against target surfaces h_target (int32 CUDA [B, X, Y]); quantised units.
+    Returns a dict: energies, aug_energies, hinge, flows, aug_flows (lists of int), heights,
+    h_hat (int32 CUDA [B, X, Y])."""
+    import torch
+
+    if cost.dim() != 4:
+        raise PogError(POG_E_INVALID, "cost must be [B, X, Y, Z]")
+    B, X, Y, Z = cost.shape
+    if tuple(h_target.shape) != (B, X, Y) or h_target.device != cost.device:
+        raise PogError(POG_E_INVALID, "h_target must be an int32 tensor [B, X, Y] on the device of cost")
+    heights = torch.empty((B, X, Y), dtype=torch.int32, device=cost.device)
+    h_hat = torch.empty((B, X, Y), dtype=torch.int32, device=cost.device)
+    arr = {k: (ctypes.c_int64 * max(B, 1))() for k in ("energies", "aug_energies", "hinge", "flows", "aug_flows")}
+    _check(load().pog_solve_batch_f32_hinge(B, _dev(cost, torch.float32, "cost"), float(scale),
+                                            _dev(h_target, torch.int32, "h_target"), int(margin), X, Y, Z, int(delta),
+                                            int(alpha), ctypes.byref(options) if options else None, _stream(stream),
+                                            arr["energies"], arr["aug_energies"], arr["hinge"], arr["flows"],
+                                            arr["aug_flows"], _dev(heights, torch.int32, "heights"),
+                                            _dev(h_hat, torch.int32, "h_hat")), "pog_solve_batch_f32_hinge")
+    out = {k: [int(v[i]) for i in range(B)] for k, v in arr.items()}
+    out["heights"] = heights
+    out["h_hat"] = h_hat
+    return out
 
 
 def pog_solve_noalloc(cost, delta: int, alpha: int, heights, options: pog_options | None = None, stream=None) -> int:

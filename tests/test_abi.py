@@ -54,6 +54,25 @@ def test_header_compiles_as_c(tmp_path):
                     str(tmp_path / "use.o")], check=True)
 
 
-def test_options_struct_layout():
-    assert ctypes.sizeof(pog.pog_options) == 32
-    assert ctypes.sizeof(pog.pog_stats_t) == 112
+def test_struct_layouts_match_the_header(tmp_path):
+    """Size and field offsets of every struct the binding mirrors, as the C compiler lays
+    them out from pog.h, against the ctypes declarations."""
+    structs = {"pog_options": pog.pog_options, "pog_stats_t": pog.pog_stats_t, "pog_volume": pog.pog_volume}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pog.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        struct, field, value = ln.split()
+        got[(struct, field)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

@@ -182,3 +182,52 @@ def test_surface_energy_kernel():
     h[0, 0, 0] = 20  # outside [0, Z)
     out = pog.pog_surface_energy(torch.from_numpy(fc).cuda(), SCALE, torch.from_numpy(h).cuda(), 300).cpu().numpy()
     assert out[0] == np.iinfo(np.int64).min
+
+
+@pytest.mark.parametrize("target", ["random", "bottom", "top", "mixed"])
+def test_warm_hinge_matches_cold_and_oracle(target):
+    """The loss-augmented solve started from the energy solve's final state gives the
+    oracle's flow, energy and surface of the augmented problem, including targets on the
+    bottom layer (its constants change) and on the top layer (no node above it)."""
+    rng = np.random.default_rng({"random": 1, "bottom": 2, "top": 3, "mixed": 4}[target])
+    specs = [synth.scaled_spec(20, 17, 24, 300 + i, stream=6000 + i) for i in range(3)]
+    fc = np.stack([synth.float_horizon_cost(s) for s in specs])
+    B, X, Y, Z = fc.shape
+    if target == "random":
+        ht = rng.integers(0, Z, size=(B, X, Y))
+    elif target == "bottom":
+        ht = np.zeros((B, X, Y))
+    elif target == "top":
+        ht = np.full((B, X, Y), Z - 1)
+    else:
+        ht = rng.choice([0, 1, Z - 2, Z - 1, Z // 2], size=(B, X, Y))
+    ht = ht.astype(np.int32)
+    delta, aq, mq = 2, 10240, 3000
+    xc = torch.from_numpy(fc).cuda()
+    htd = torch.from_numpy(ht).cuda()
+    outs = [pog.pog_solve_batch_f32_hinge(xc, SCALE, htd, mq, delta, aq, pog.make_options(flags=f))
+            for f in (0, pog.POG_FLAG_COLD_HINGE)]
+    for b in range(B):
+        cq = quantise(fc[b])
+        aug = cq.copy()
+        np.put_along_axis(aug, ht[b][:, :, None], np.take_along_axis(cq, ht[b][:, :, None], 2) + mq, axis=2)
+        ref = oracle.solve(cq, delta, aq)
+        ref_aug = oracle.solve(aug, delta, aq)
+        e_aug, _ = oracle.energy(aug, ref_aug.heights, delta, aq)
+        e_t, _ = oracle.energy(cq, ht[b], delta, aq)
+        for out in outs:
+            assert out["flows"][b] == ref.flow
+            assert out["aug_flows"][b] == ref_aug.flow
+            assert out["aug_energies"][b] == e_aug
+            assert out["hinge"][b] == e_t - (e_aug - mq * X * Y)
+            np.testing.assert_array_equal(out["heights"][b].cpu().numpy(), ref.heights)
+            np.testing.assert_array_equal(out["h_hat"][b].cpu().numpy(), ref_aug.heights)
+
+
+def test_hinge_rejects_targets_outside_the_volume():
+    fc = torch.zeros((1, 4, 5, 6), device="cuda")
+    ht = torch.zeros((1, 4, 5), dtype=torch.int32, device="cuda")
+    ht[0, 1, 2] = 6
+    with pytest.raises(pog.PogError) as ei:
+        pog.pog_solve_batch_f32_hinge(fc, SCALE, ht, 1024, 1, 0)
+    assert ei.value.status == pog.POG_E_INVALID

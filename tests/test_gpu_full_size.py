@@ -73,3 +73,46 @@ def test_uneven_batch_matches_stored_oracle():
         assert fl == r["flow"], v.name
         h = np.ascontiguousarray(h.cpu().numpy(), dtype=np.int32)
         assert hashlib.sha256(h.tobytes()).hexdigest() == r["heights_sha256"], v.name
+
+
+def test_differentiable_workload_matches_stored_oracle():
+    """The 16 float volumes of 128^3 (delta 2, alpha 10, hinge margin 1 against a flat
+    target): energies, optimal and loss-augmented surfaces, hinge losses and the gradient
+    of E* + L, against the oracle's stored results (tests/golden/diff.json). The
+    loss-augmented solve runs warm (from the energy solve's state) in the autograd path and
+    cold through the raw entry point; both must give the oracle's values."""
+    from paper_2601_17026_gb300 import autograd as pag
+
+    with open(os.path.join(GOLDEN, "diff.json")) as f:
+        ref = json.load(f)["volumes"]
+    fc = synth.diff_volumes_f32()
+    ht = synth.diff_target()
+    B, X, Y, Z = fc.shape
+    assert len(ref) == B
+    x = torch.from_numpy(fc).cuda().requires_grad_(True)
+    htd = torch.from_numpy(ht).cuda()
+    e, loss, h, hh = pag.solve_with_hinge(x, htd, synth.DIFF_DELTA, synth.DIFF_ALPHA, synth.DIFF_MARGIN)
+    (e.sum() + loss.sum()).backward()
+
+    def sha(t):
+        return hashlib.sha256(np.ascontiguousarray(t.cpu().numpy(), dtype=np.int32).tobytes()).hexdigest()
+
+    for b, r in enumerate(ref):
+        assert e[b].item() * 1024 == r["energy"], b
+        assert loss[b].item() * 1024 == r["hinge_q"], b
+        assert sha(h[b]) == r["heights_sha256"], b
+        assert sha(hh[b]) == r["aug_heights_sha256"], b
+    # gradient of E* + L: onehot(h*) + onehot(h_t) - onehot(h_hat), exactly
+    zs = torch.arange(Z, device="cuda", dtype=torch.int32)
+    want = ((h[..., None] == zs).float() + (htd[..., None] == zs).float() - (hh[..., None] == zs).float())
+    assert torch.equal(x.grad, want)
+    # the raw entry point, warm and cold: flow values of both graphs as well
+    xc = torch.from_numpy(fc).cuda()
+    for flags in (0, pog.POG_FLAG_COLD_HINGE):
+        out = pog.pog_solve_batch_f32_hinge(xc, 1024.0, htd, 1024, synth.DIFF_DELTA, 10240,
+                                            pog.make_options(flags=flags))
+        for b, r in enumerate(ref):
+            assert out["flows"][b] == r["flow"] and out["aug_flows"][b] == r["aug_flow"], (flags, b)
+            assert out["energies"][b] == r["energy"] and out["aug_energies"][b] == r["aug_energy"], (flags, b)
+            assert out["hinge"][b] == r["hinge_q"], (flags, b)
+            assert sha(out["h_hat"][b]) == r["aug_heights_sha256"], (flags, b)

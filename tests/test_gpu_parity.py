@@ -130,6 +130,7 @@ def test_certificate_export_state():
             h = pog.pog_surface(g).cpu().numpy()
             st = pog.pog_export_state(g)
         certificate.check(cost, delta, alpha, st, flow, h)
+        assert oracle.certify(cost, delta, alpha, st, flow, h) == 0
         assert oracle.cut_capacity(cost, h, delta, alpha) == flow
 
 

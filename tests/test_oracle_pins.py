@@ -14,6 +14,7 @@ import sys
 import numpy as np
 import pytest
 
+import certificate
 import oracle
 import pins
 from paper_2601_17026_gb300 import synth
@@ -335,3 +336,69 @@ def test_dinic_matches_library_edmonds_karp(seed):
     ref = csgraph.maximum_flow(g, s, t, method="edmonds_karp").flow_value
     assert ref < inf  # no infinite path from s to t
     assert oracle.solve(cost, delta, alpha).flow == ref
+
+
+# --- the certificate's accept path on states known to be optimal -----------------------
+
+CERT_CASES = [((3, 4, 6), 0, 0), ((3, 4, 6), 1, 3), ((4, 3, 7), 2, 17), ((5, 5, 8), 2, 0), ((2, 6, 5), 5, 4),
+              ((6, 2, 9), 3, 50), ((4, 4, 4), 1, 1)]
+
+
+@pytest.mark.parametrize("shape,delta,alpha", CERT_CASES)
+def test_certificate_accepts_the_oracles_own_optimal_state(shape, delta, alpha):
+    """The oracle's final Dinic flow, written in the exported-state layout (bottom layer
+    as part of the source), is a maximum preflow whose cut is the minimal one: the
+    certificate must accept it, and so must the independent numpy certificate."""
+    rng = np.random.default_rng(hash((shape, delta, alpha)) % (2**32))
+    nontrivial = 0
+    for kind in ("uniform", "horizon"):
+        if kind == "uniform":
+            cost = rng.integers(-40, 81, size=shape).astype(np.int32)
+        else:
+            cost = synth.horizon_cost(synth.scaled_spec(*shape, seed=int(rng.integers(1 << 30)), stream=3))
+        flow, h, st = oracle.solve_state(cost, delta, alpha)
+        ref = oracle.solve(cost, delta, alpha)
+        assert flow == ref.flow
+        np.testing.assert_array_equal(h, ref.heights)
+        assert oracle.certify(cost, delta, alpha, st, flow, h) == 0
+        certificate.check(cost, delta, alpha, st, flow, h)
+        nontrivial += int(st["excess"].any() and (st["fdown"].any() or st["fhard"].any() or st["gsoft"].any()))
+    assert nontrivial >= 1, "the states should carry excess and arc flow"
+
+
+def test_certificate_rejects_one_word_perturbations_of_an_optimal_state():
+    """Each check of the certificate catches a one-word change of an optimal state."""
+    cost = synth.horizon_cost(synth.scaled_spec(6, 5, 12, seed=77, stream=5))
+    d, a = 2, 5
+    flow, h, st = oracle.solve_state(cost, d, a)
+    assert oracle.certify(cost, d, a, st, flow, h) == 0
+    X, Y, Z = cost.shape
+    w = np.diff(cost.astype(np.int64), axis=2, prepend=0).reshape(-1)  # w(z) for z >= 1
+    above = np.arange(X * Y * Z) % Z != 0
+
+    def perturbed(key, i, delta_word):
+        bad = {k: v.copy() for k, v in st.items()}
+        bad[key][i] += delta_word
+        return bad
+
+    # 10: a sink residual above the sink arc's capacity
+    v = int(np.flatnonzero(above & (w > 0))[0])
+    assert oracle.certify(cost, d, a, perturbed("sink", v, int(w[v]) - int(st["sink"][v]) + 1), flow, h) == 10
+    # 11: one unit of excess too many
+    v = int(np.flatnonzero(above)[0])
+    assert oracle.certify(cost, d, a, perturbed("excess", v, 1), flow, h) == 11
+    # 12: the reported flow value off by one
+    assert oracle.certify(cost, d, a, st, flow + 1, h) == 12
+    # 13: one cut mark flipped
+    v = int(np.flatnonzero(above & (st["in_cut"] == 1))[0])
+    assert oracle.certify(cost, d, a, perturbed("in_cut", v, -1), flow, h) == 13
+    # 14: one height off the top of its column's cut
+    bad_h = h.copy()
+    bad_h.reshape(-1)[0] += 1 if h.reshape(-1)[0] + 1 < Z else -1
+    assert oracle.certify(cost, d, a, st, flow, bad_h) == 14
+    # 15: a feasible but not maximum preflow, one unit taken back from a saturated sink
+    #     arc of a cut node into its excess: every other check still holds
+    v = int(np.flatnonzero(above & (st["in_cut"] == 1) & (w > 0) & (st["sink"] < w))[0])
+    bad = perturbed("sink", v, 1)
+    bad["excess"][v] += 1
+    assert oracle.certify(cost, d, a, bad, flow - 1, h) == 15

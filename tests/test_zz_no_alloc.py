@@ -41,6 +41,27 @@ def test_noalloc_matches_allocating_path_twice_in_a_row():
         np.testing.assert_array_equal(got[1], ref[1])
 
 
+def test_noalloc_matches_the_oracle():
+    """Against the CPU oracle directly, not only against the allocating GPU path."""
+    import oracle
+
+    for seed, (X, Y, Z), delta, alpha in [(43, (24, 20, 40), 2, 25), (44, (17, 33, 36), 1, 0)]:
+        cost = synth.horizon_cost(synth.scaled_spec(X, Y, Z, seed, stream=seed))
+        got = _noalloc(torch.from_numpy(cost).cuda(), delta, alpha)
+        ref = oracle.solve(cost, delta, alpha)
+        assert got[0] == ref.flow
+        np.testing.assert_array_equal(got[1], ref.heights)
+
+
+def test_noalloc_rejects_a_heights_buffer_of_the_wrong_shape():
+    cost = torch.zeros((6, 5, 8), dtype=torch.int32, device="cuda")
+    for bad in (torch.empty((6, 4), dtype=torch.int32, device="cuda"), torch.empty((30,), dtype=torch.int32,
+                                                                                   device="cuda")):
+        with pytest.raises(pog.PogError) as ei:
+            pog.pog_solve_noalloc(cost, 1, 0, bad)
+        assert ei.value.status == pog.POG_E_INVALID
+
+
 def test_noalloc_rejects_volumes_beyond_the_scratch():
     big = torch.zeros((128, 128, 64), dtype=torch.int32, device="cuda")  # 1M nodes > limit
     heights = torch.empty((128, 128), dtype=torch.int32, device="cuda")
