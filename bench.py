@@ -152,6 +152,36 @@ def algorithmic_bytes(N, alpha, tiles_per_sweep, scans_per_sweep):
     }, S
 
 
+# DRAM bytes per unit of work of the two dominant kernels, from ncu captures of the
+# 256x256x384 crop of the benchmark volume (dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch divided by the launch's units: tile visits for the tiled sweep, nodes
+# for the global relabel), with the SHA-256 prefix of the kernel source they were taken
+# on. A kernel whose source changed since reports no traffic.
+MEASURED_TRAFFIC = {}
+
+
+def _source_sha(kernel):
+    import hashlib
+
+    src = {"k_tile_push_relabel": "pog_tile.cu", "k_global_relabel": "pog_bfs.cu"}.get(kernel)
+    if src is None:
+        return None
+    h = hashlib.sha256()
+    for name in (src, "pog_internal.cuh"):  # the kernel's file and the arc enumeration it uses
+        with open(os.path.join(ROOT, "paper_2601_17026_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, units):
+    """DRAM bytes of one launch processing `units` units, scaled from the ncu capture, or
+    None when there is no capture of the current kernel source."""
+    entry = MEASURED_TRAFFIC.get(kernel)
+    if not entry or entry["source_sha"] != _source_sha(kernel) or not units:
+        return None
+    return entry["bytes_per_unit"] * units
+
+
 def run_ours(args):
     import torch
 
@@ -236,7 +266,7 @@ def run_ours(args):
     per_step = ms / args.steps
     value = job_throughput(ws, N, args.steps, ms)
     e2e_value = job_throughput(ws, N, args.steps, e2e_ms)
-    # roofline of the dominant kernel family, timed live with events on the solve stream
+    # roofline of the two dominant kernel families, timed live with events on the solve stream
     tiles_per_sweep = sum(s["tiles_visited"] for s in stats) / max(sum(s["sweeps"] for s in stats), 1)
     scans_per_sweep = sum(s["rounds"] - 1 for s in stats) / max(sum(s["sweeps"] for s in stats), 1)
     bytes_per, S = algorithmic_bytes(N, vol.alpha, tiles_per_sweep, scans_per_sweep)
@@ -244,12 +274,23 @@ def run_ours(args):
            "build": ("build_ms", None)}
     tot = {k: sum(s[v[0]] for s in stats) for k, v in fam.items()}
     launches = {k: (sum(s[v[1]] for s in stats) if v[1] else len(stats)) for k, v in fam.items()}
-    dom = max(tot, key=tot.get)
-    avg_ms = tot[dom] / max(launches[dom], 1)
     peak, peak_src = _peaks()
-    achieved = bytes_per[dom] / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
     kernel_name = {"sweep": "k_tile_push_relabel", "bfs": "k_global_relabel", "cut": "k_cut_reach",
-                   "build": "k_build"}[dom]
+                   "build": "k_build"}
+    units = {"sweep": tiles_per_sweep, "bfs": N}
+
+    def roofline(k):
+        avg_ms = tot[k] / max(launches[k], 1)
+        achieved = bytes_per[k] / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+        traffic = measured_traffic(kernel_name[k], units.get(k, 0))
+        return {"bound": "hbm", "kernel": kernel_name[k], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None if traffic is None else int(traffic),
+                "traffic_ratio": None if traffic is None else round(traffic / bytes_per[k], 2),
+                "peak_source": peak_src, "bytes_per_launch": int(bytes_per[k]),
+                "launches_per_step": launches[k] / len(stats), "avg_launch_ms": round(avg_ms, 5)}
+
+    dom = max(("sweep", "bfs"), key=tot.get)
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -261,13 +302,14 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * X * Y + 8},
-        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                     "peak_source": peak_src, "bytes_per_launch": bytes_per[dom],
-                     "launches_per_step": launches[dom] / len(stats), "avg_launch_ms": round(avg_ms, 5)},
+        "roofline": roofline(dom),
+        "rooflines": {kernel_name[k]: roofline(k) for k in ("sweep", "bfs")},
         "kernel_ms_per_step": {k: round(v / len(stats), 3) for k, v in tot.items()},
         "solver": {k: st0[k] for k in ("rounds", "sweeps", "bfs_passes", "cut_passes", "gaps", "active_initial",
                                         "tiles_visited")},
+        "solver_spread": {"rounds": [int(s["rounds"]) for s in stats],
+                          "ms_sweep": [round(s["sweep_ms"], 1) for s in stats],
+                          "ms_relabel": [round(s["bfs_ms"], 1) for s in stats]},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks.summary(),
         "flow": flow,
@@ -277,21 +319,39 @@ def run_ours(args):
     if args.extras:
         line["batched"] = batched_leg(args)
         line["differentiable"] = differentiable_leg(args)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline_batched"] = cpu_baseline_batched(args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
-def batched_leg(args, warmup=1, steps=1):
-    """The 64 uneven volumes through pog_solve_batch (inputs resident), aggregate Mnodes/s;
-    flows checked against the oracle's stored values when tests/golden/batch.json exists."""
+def _timed_median(fn, warmup, steps):
+    """Median wall time (s) of `steps` calls after `warmup` calls, device synchronised
+    around each, and the last call's result."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    times, out = [], None
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    return statistics.median(times), times, out
+
+
+def batched_leg(args, warmup=1, steps=3):
+    """The 64 uneven volumes through pog_solve_batch (inputs resident), aggregate Mnodes/s
+    (median of `steps` solves); flows and surfaces checked against the oracle's stored
+    values (tests/golden/batch.json)."""
     import hashlib
 
     import torch
 
-    from paper_2601_17026_gb300 import pog, synth
-
-    from paper_2601_17026_gb300 import autotune
+    from paper_2601_17026_gb300 import autotune, pog, synth
 
     vols = synth.batch_volumes()
     costs = [torch.from_numpy(v.cost).cuda() for v in vols]
@@ -299,17 +359,12 @@ def batched_leg(args, warmup=1, steps=1):
     alphas = [v.alpha for v in vols]
     params = autotune.batch_params("uneven-64")
     opts = pog.make_options(**params)
-    for _ in range(warmup):
-        pog.pog_solve_batch(costs, deltas, alphas, opts)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(steps):
-        flows, heights = pog.pog_solve_batch(costs, deltas, alphas, opts)
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t) / steps
+    dt, times, (flows, heights) = _timed_median(lambda: pog.pog_solve_batch(costs, deltas, alphas, opts), warmup,
+                                                steps)
     n = sum(v.n for v in vols)
-    out = {"value": round(n / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2), "volumes": len(vols),
-           "nodes": n, "driver": "one solve of the disjoint union of the volumes; finished volumes leave at each global relabel",
+    out = {"value": round(n / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2),
+           "ms_all_steps": [round(t * 1e3, 1) for t in times], "volumes": len(vols), "nodes": n,
+           "driver": "one solve of the disjoint union of the volumes; finished volumes leave at each global relabel",
            "params": params}
     gold = os.path.join(ROOT, "tests", "golden", "batch.json")
     if os.path.exists(gold):
@@ -323,9 +378,13 @@ def batched_leg(args, warmup=1, steps=1):
     return out
 
 
-def differentiable_leg(args, warmup=1, steps=1):
-    """16 float volumes of 128^3: quantise + solve + structured-hinge second solve + one-hot
-    backward, aggregate Mnodes/s of the volumes processed."""
+def differentiable_leg(args, warmup=1, steps=3):
+    """16 float volumes of 128^3: quantise + energy solve + loss-augmented solve (warm,
+    from the energy solve's state) + structured-hinge loss + one-hot backward, aggregate
+    Mnodes/s of the volumes processed (median of `steps`); every energy, loss and surface
+    checked against the oracle's stored values (tests/golden/diff.json)."""
+    import hashlib
+
     import torch
 
     from paper_2601_17026_gb300 import autograd as pag
@@ -333,24 +392,49 @@ def differentiable_leg(args, warmup=1, steps=1):
 
     fc = torch.from_numpy(synth.diff_volumes_f32()).cuda()
     B, X, Y, Z = fc.shape
-    ht = torch.full((B, X, Y), Z // 2, dtype=torch.int32, device="cuda")  # a flat target surface
+    ht = torch.from_numpy(synth.diff_target(B, X)).cuda()
 
     def step():
         x = fc.clone().requires_grad_(True)
-        e, loss, h, hh = pag.solve_with_hinge(x, ht, synth.DIFF_DELTA, synth.DIFF_ALPHA)
+        e, loss, h, hh = pag.solve_with_hinge(x, ht, synth.DIFF_DELTA, synth.DIFF_ALPHA, synth.DIFF_MARGIN)
         (e.sum() + loss.sum()).backward()
-        return x.grad
+        return e, loss, h, hh, x.grad
 
-    for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(steps):
-        step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t) / steps
-    return {"value": round(B * X * Y * Z / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2),
-            "step": "forward (energy solve + loss-augmented solve) + backward", "volumes": B}
+    dt, times, (e, loss, h, hh, grad) = _timed_median(step, warmup, steps)
+    out = {"value": round(B * X * Y * Z / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2),
+           "ms_all_steps": [round(t * 1e3, 1) for t in times],
+           "step": "forward (energy solve + warm loss-augmented solve + hinge) + backward", "volumes": B}
+    gold = os.path.join(ROOT, "tests", "golden", "diff.json")
+    if os.path.exists(gold):
+        with open(gold) as f:
+            ref = json.load(f)["volumes"]
+        sha = lambda t: hashlib.sha256(t.cpu().numpy().astype(np.int32).tobytes()).hexdigest()  # noqa: E731
+        ok = sum(int(e[b].item() * 1024 == r["energy"] and loss[b].item() * 1024 == r["hinge_q"]
+                     and sha(h[b]) == r["heights_sha256"] and sha(hh[b]) == r["aug_heights_sha256"])
+                 for b, r in enumerate(ref))
+        zs = torch.arange(Z, device="cuda", dtype=torch.int32)
+        want = (h[..., None] == zs).float() + (ht[..., None] == zs).float() - (hh[..., None] == zs).float()
+        out["oracle_parity"] = (f"{ok}/{len(ref)} volumes bit-exact (energy, hinge, both surfaces); gradient "
+                                f"{'exact' if torch.equal(grad, want) else 'DIFFERS'}")
+    return out
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
 
 
 def _crop(vol, X, Y):
@@ -367,9 +451,35 @@ def cpu_baseline(args, vol, sample_xy=32):
     t = time.perf_counter()
     oracle.solve(crop.cost, crop.delta, crop.alpha)
     dt = time.perf_counter() - t
+    nproc, model = host_cpu()
     return {"value": round(crop.n / dt / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host_cores": nproc, "cpu_model": model,
             "sample": f"{sample_xy}x{sample_xy}x{vol.cost.shape[2]} crop (x,y < {sample_xy}) of the workload, "
                       f"{crop.n} nodes, {dt:.1f} s single-threaded explicit-edge Dinic"}
+
+
+def cpu_baseline_batched(args, count=16, sample_xy=32):
+    """The oracle on a thread pool of min(volumes, cores) threads over a bounded sample of
+    the uneven batch: the x,y < 32 crops of its first `count` volumes."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    from paper_2601_17026_gb300 import synth
+
+    vols = [_crop(v, sample_xy, sample_xy) for v in synth.batch_volumes(limit=count)]
+    nproc, model = host_cpu()
+    workers = max(1, min(len(vols), nproc))
+    oracle.build()
+    t = time.perf_counter()
+    with ThreadPoolExecutor(workers) as ex:  # the oracle releases the GIL inside C
+        list(ex.map(lambda v: oracle.solve(v.cost, v.delta, v.alpha), vols))
+    dt = time.perf_counter() - t
+    n = sum(v.n for v in vols)
+    return {"value": round(n / dt / 1e6, 5), "unit": UNIT, "cores": workers, "kind": "oracle",
+            "host_cores": nproc, "cpu_model": model,
+            "sample": f"x,y < {sample_xy} crops of the first {len(vols)} volumes of the 64-volume batch "
+                      f"({n} nodes), {dt:.1f} s on {workers} threads"}
 
 
 def run_reference(args):
@@ -396,6 +506,7 @@ def run_reference(args):
         "config": {"workload": f"{X}x{Y}x{Z} layered-horizon volume, delta={vol.delta}, alpha={vol.alpha}",
                    "sample": "32x32 crop per step"},
         "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host_cores": host_cpu()[0], "cpu_model": host_cpu()[1],
                          "sample": f"32x32x{Z} crop of the workload ({crop.n} nodes) per step"},
         "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

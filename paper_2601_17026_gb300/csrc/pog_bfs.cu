@@ -111,6 +111,79 @@ __device__ __forceinline__ void gather_out_any(const Grid &g, int u, int x, int 
     else gather_out<false, RO, true>(g, u, x, y, z, h, far);
 }
 
+// Top-down expansion of frontier node v: claim, in the visited bitmap, every in-arc tail
+// u (arc u -> v residual) not labelled yet; returns the mask of slots won (slots as in
+// gather_in, tails in `node`, volume-local). The tails' bitmap words are read first (from
+// L2); a residual word is then loaded only for an arc whose tail is still unvisited and
+// whose residual is not known (infinite arcs are residual), so most of a node's scattered
+// arc words are never fetched: in a search wave the greater part of the tails is already
+// labelled.
+template <bool SOFT>
+__device__ __forceinline__ unsigned td_claim(const Grid &g, int v, int x, int y, int z, unsigned *visit, int base,
+                                             int *node) {
+    const int D = g.delta;
+    unsigned exist = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) node[k] = v;
+    if (z + 1 < g.Z) {
+        node[0] = v + 1;  // down arc of v+1 (infinite)
+        exist |= 1u;
+    }
+    if (z >= 2) {
+        node[1] = v - 1;  // up arc of v-1: residual fdn[v]
+        exist |= 2u;
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        bool ok;
+        const int off = nb_offset(g, x, y, d, ok);
+        if (!ok) continue;
+        if (z + D < g.Z) {
+            node[2 + 3 * d] = v + off + D;  // hard arc of (q, z+D) (infinite)
+            exist |= 1u << (2 + 3 * d);
+        }
+        if (z - D >= 1) {
+            node[3 + 3 * d] = v + off - D;  // reverse of v's hard arc: residual fh[d][v]
+            exist |= 1u << (3 + 3 * d);
+        }
+        if (SOFT) {
+            node[4 + 3 * d] = v + off;  // soft arc of (q, z)
+            exist |= 1u << (4 + 3 * d);
+        }
+    }
+    unsigned word[kMaxArcs];
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k)
+        word[k] = (exist >> k & 1u) ? (unsigned)ldcg(reinterpret_cast<const int32_t *>(visit) + ((base + node[k]) >> 5))
+                                    : 0xffffffffu;
+    unsigned cand = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) cand |= ((word[k] >> ((base + node[k]) & 31)) & 1u) ? 0u : 1u << k;
+    if (!cand) return 0;
+    int res[kMaxArcs];
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) res[k] = 1;
+    if (cand & 2u) res[1] = __ldg(g.fdn + v);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        if (cand >> (3 + 3 * d) & 1u) res[3 + 3 * d] = __ldg(g.fh[d] + v);
+        if (SOFT && (cand >> (4 + 3 * d) & 1u))
+            res[4 + 3 * d] = (d & 1) ? g.alpha + __ldg(g.gs[d >> 1] + v) : g.alpha - __ldg(g.gs[d >> 1] + node[4 + 3 * d]);
+    }
+    unsigned old[kMaxArcs];
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k) {
+        const int un = base + node[k];
+        const unsigned bit = 1u << (un & 31);
+        old[k] = ((cand >> k & 1u) && res[k] > 0) ? atomicOr(visit + (un >> 5), bit) : bit;
+    }
+    unsigned won = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxArcs; ++k)
+        if (!(old[k] & (1u << ((base + node[k]) & 31)))) won |= 1u << k;
+    return won;
+}
+
 // Bottom-up test of an unlabelled node u: does one of its residual out-arcs end at a
 // node of `level`? The far ends' labels are loaded first; residuals only for the arcs
 // whose far end is at `level` (most nodes have none).
@@ -270,24 +343,12 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
                     const int v = uv - base;
                     int x, y, z;
                     decode(g, v, x, y, z);
-                    // residuals of the in-arcs and the visited words of their tails, in one
-                    // round trip (the words come from the bitmap in L2, not from the labels)
-                    gather_in_any<true>(g, v, x, y, z, hd, visit, base);
-                    unsigned old[kMaxArcs];
+                    won = g.gs[0] ? td_claim<true>(g, v, x, y, z, visit, base, hd.node)
+                                  : td_claim<false>(g, v, x, y, z, visit, base, hd.node);
 #pragma unroll
                     for (int k = 0; k < kMaxArcs; ++k) {
-                        const int un = base + hd.node[k];
-                        const unsigned bit = 1u << (un & 31);
-                        old[k] = (hd.res[k] > 0 && !(hd.lab[k] & bit)) ? atomicOr(visit + (un >> 5), bit) : bit;
-                    }
-#pragma unroll
-                    for (int k = 0; k < kMaxArcs; ++k) {
-                        const int un = base + hd.node[k];
-                        if (!(old[k] & (1u << (un & 31)))) {
-                            won |= 1u << k;
-                            g.lab[hd.node[k]] = level + 1;
-                        }
-                        hd.node[k] = un;  // to union indices
+                        if (won >> k & 1u) g.lab[hd.node[k]] = level + 1;
+                        hd.node[k] += base;  // to union indices
                     }
                 }
                 warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
