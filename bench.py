@@ -319,6 +319,7 @@ def run_ours(args):
     if args.extras:
         line["batched"] = batched_leg(args)
         line["differentiable"] = differentiable_leg(args)
+        line["narrow_band"] = narrow_band_leg(args)
         if not args.no_cpu_baseline:
             line["cpu_baseline_batched"] = cpu_baseline_batched(args)
     print(json.dumps(line), flush=True)
@@ -416,6 +417,56 @@ def differentiable_leg(args, warmup=1, steps=3):
         want = (h[..., None] == zs).float() + (ht[..., None] == zs).float() - (hh[..., None] == zs).float()
         out["oracle_parity"] = (f"{ok}/{len(ref)} volumes bit-exact (energy, hinge, both surfaces); gradient "
                                 f"{'exact' if torch.equal(grad, want) else 'DIFFERS'}")
+    return out
+
+
+def narrow_band_leg(args, warmup=1, steps=3):
+    """The narrow band of the 512x512x384 volume around 64 landmarks on its central
+    horizon (stick 16, band factor 2: 65 rows, 17.0M band nodes): band construction +
+    solve + image heights, Mnodes/s of band nodes (median of `steps`). The band volume is
+    checked against the oracle's construction bit for bit, and its solve by the oracle's
+    O(N) certificate (the band is too large for Dinic here)."""
+    import torch
+
+    import oracle
+    from oracle import band as oband
+
+    from paper_2601_17026_gb300 import autotune, pog, synth
+
+    spec = synth.spec_seismic()
+    cost_np = synth.horizon_cost(spec)
+    lm_np = synth.horizon_landmarks(spec, 8)
+    cost = torch.from_numpy(cost_np).cuda()
+    lm = torch.from_numpy(lm_np).cuda()
+    stick, factor, outside = synth.BAND_STICK, synth.BAND_FACTOR, synth.BAND_OUTSIDE
+    half = stick * factor
+    X, Y = cost.shape[:2]
+    Zb = 2 * half + 1
+    opts = pog.make_options(**autotune.tuned_params(X, Y, Zb, 3, 50))
+
+    def step(export=False):
+        b, c = pog.pog_narrow_band(cost, lm, stick, factor, outside)
+        with pog.pog_build(b, 3, 50, opts) as g:
+            flow = pog.pog_maxflow(g)
+            hb = pog.pog_surface(g)
+            himg = pog.pog_band_heights(hb, c, half)
+            st = pog.pog_export_state(g) if export else None
+        return b, c, flow, hb, himg, st
+
+    dt, times, _ = _timed_median(step, warmup, steps)
+    b, c, flow, hb, himg, st = step(export=args.band_certify)  # untimed: the solve that is certified
+    n = X * Y * Zb
+    out = {"value": round(n / dt / 1e6, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 2),
+           "ms_all_steps": [round(t * 1e3, 1) for t in times], "band_nodes": n, "rows": Zb, "landmarks": len(lm_np),
+           "step": "band construction + solve (build, max-flow, surface) + image heights"}
+    rb, rc = oband.narrow_band(cost_np, lm_np, stick, factor, outside)
+    same = torch.equal(b.cpu(), torch.from_numpy(rb)) and np.array_equal(c.cpu().numpy(), rc)
+    cert = "not run"
+    if st is not None:
+        rcode = oracle.certify(rb, 3, 50, st, flow, hb.cpu().numpy())
+        cert = "optimal (certificate 0)" if rcode == 0 else f"certificate failed ({rcode})"
+    out["oracle_parity"] = (f"band volume {'bit-exact' if same else 'DIFFERS'} vs the oracle's construction; "
+                            f"band solve {cert}")
     return out
 
 
@@ -526,6 +577,8 @@ def main():
     ap.add_argument("--extras", dest="extras", action="store_true", default=True,
                     help="also time the batched and differentiable workloads (default)")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-band-certify", dest="band_certify", action="store_false", default=True,
+                    help="skip the O(N) certificate of the narrow-band solve")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

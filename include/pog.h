@@ -306,6 +306,38 @@ POG_API pog_status pog_solve_batch_f32_hinge(int32_t B, const float *cost_dev, f
                                              int32_t *heights_dev, int32_t *h_hat_dev);
 
 /*
+ * Narrow-band construction (Section 3.4): the structured graph built around landmark
+ * points on a horizon. In each column it spans `half` = stick * band_factor rows below
+ * and above a center surface through the landmarks, Zb = 2 * half + 1 rows in all.
+ * The paper gives no formula for that surface; here it is the inverse-squared-distance
+ * average of the landmark heights, rounded half up:
+ *   center(x, y) = floor(sum_i w_i z_i / sum_i w_i + 0.5),  w_i = 1 / ((x-x_i)^2 + (y-y_i)^2),
+ * in float64 with every operation rounded to nearest, summed in landmark order (the
+ * height z_i of the first landmark on the column itself when there is one), clamped to
+ * [0, Zi). The band cost volume is
+ *   band(x, y, k) = cost(x, y, center - half + k)   if 0 <= center - half + k < Zi,
+ *                   outside_cost                     otherwise,
+ * a volume of X * Y * Zb nodes for pog_build / pog_solve_noalloc; its surface maps back to
+ * image heights with pog_band_heights.
+ *   cost_dev      : device int32 [X][Y][Zi], the image cost volume.
+ *   landmarks_dev : device int32 [L][3], (x, y, z) of each landmark, 0 <= z < Zi; L >= 1.
+ *   stick, band_factor : >= 0 and >= 1; X * Y * Zb < 2^31.
+ *   outside_cost  : |outside_cost| < 2^30, the cost of rows outside the image.
+ *   band_dev      : device int32 [X][Y][Zb] (out).   center_dev : device int32 [X][Y] (out).
+ * Enqueued on `stream`.
+ */
+POG_API pog_status pog_narrow_band(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Zi,
+                                   const int32_t *landmarks_dev, int32_t L, int32_t stick, int32_t band_factor,
+                                   int32_t outside_cost, void *stream, int32_t *band_dev, int32_t *center_dev);
+
+/*
+ * Image heights of a surface solved on a narrow band: h_img = center - half + h_band.
+ * Device int32 [X][Y] each. Enqueued on `stream`.
+ */
+POG_API pog_status pog_band_heights(const int32_t *h_band_dev, const int32_t *center_dev, int32_t X, int32_t Y,
+                                    int32_t half, void *stream, int32_t *h_img_dev);
+
+/*
  * Solve one volume without allocating anything (the paper has no counterpart; this
  * entry point exists for callers of this library, not for the method).
  *

@@ -34,7 +34,7 @@ POG_FLAG_COLD_HINGE = 32
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
             "pog_surface_energy", "pog_solve_batch", "pog_solve_batch_f32", "pog_solve_batch_f32_hinge",
-            "pog_solve_noalloc"]
+            "pog_narrow_band", "pog_band_heights", "pog_solve_noalloc"]
 
 
 class PogError(RuntimeError):
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
             "pog_solve_batch_f32": [i32, vp, f32, vp, i32, i32, i32, i32, i32, i32, opts, vp, i64p, i64p, vp],
             "pog_solve_batch_f32_hinge": [i32, vp, f32, vp, i32, i32, i32, i32, i32, i32, opts, vp, i64p, i64p, i64p,
                                           i64p, i64p, vp, vp],
+            "pog_narrow_band": [vp, i32, i32, i32, vp, i32, i32, i32, i32, vp, vp, vp],
+            "pog_band_heights": [vp, vp, i32, i32, i32, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -373,6 +375,39 @@ def pog_solve_batch_f32_hinge(cost, scale: float, h_target, margin: int, delta: 
     out = {k: [int(v[i]) for i in range(B)] for k, v in arr.items()}
     out["heights"] = heights
     out["h_hat"] = h_hat
+    return out
+
+
+def pog_narrow_band(cost, landmarks, stick: int, band_factor: int, outside_cost: int, stream=None):
+    """Band cost volume int32 CUDA [X, Y, 2*half+1] and center surface int32 CUDA [X, Y] of
+    an image cost volume [X, Y, Zi] around landmarks (int32 CUDA [L, 3] of x, y, z);
+    half = stick * band_factor."""
+    import torch
+
+    if cost.dim() != 3 or landmarks.dim() != 2 or landmarks.shape[1] != 3 or landmarks.device != cost.device:
+        raise PogError(POG_E_INVALID, "cost must be [X, Y, Zi] and landmarks [L, 3] on the same device")
+    X, Y, Zi = cost.shape
+    half = int(stick) * int(band_factor)
+    band = torch.empty((X, Y, 2 * half + 1), dtype=torch.int32, device=cost.device)
+    center = torch.empty((X, Y), dtype=torch.int32, device=cost.device)
+    _check(load().pog_narrow_band(_dev(cost, torch.int32, "cost"), X, Y, Zi, _dev(landmarks, torch.int32, "landmarks"),
+                                  landmarks.shape[0], int(stick), int(band_factor), int(outside_cost), _stream(stream),
+                                  _dev(band, torch.int32, "band"), _dev(center, torch.int32, "center")),
+           "pog_narrow_band")
+    return band, center
+
+
+def pog_band_heights(h_band, center, half: int, out=None, stream=None):
+    """Image heights center - half + h_band (int32 CUDA [X, Y])."""
+    import torch
+
+    if tuple(h_band.shape) != tuple(center.shape) or h_band.dim() != 2:
+        raise PogError(POG_E_INVALID, "h_band and center must both be [X, Y]")
+    X, Y = center.shape
+    if out is None:
+        out = torch.empty((X, Y), dtype=torch.int32, device=center.device)
+    _check(load().pog_band_heights(_dev(h_band, torch.int32, "h_band"), _dev(center, torch.int32, "center"), X, Y,
+                                   int(half), _stream(stream), _dev(out, torch.int32, "out")), "pog_band_heights")
     return out
 
 

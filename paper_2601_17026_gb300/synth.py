@@ -268,3 +268,22 @@ def diff_target(count: int = 16, size: int = 128) -> np.ndarray:
     """int32 [B, S, S]: the hinge target surface of the differentiable workload, flat at
     height S/2 in every column (feasible for any delta)."""
     return np.full((count, size, size), size // 2, dtype=np.int32)
+
+
+def horizon_landmarks(spec: HorizonSpec, grid: int = 8) -> np.ndarray:
+    """int32 [grid*grid, 3]: landmark points (x, y, z) on the central horizon of a volume,
+    z = round(centre + amp*sin(2 pi x/px)*cos(2 pi y/py)), at a grid x grid lattice of
+    columns (cell centres), as a user would place them on a horizon of the image."""
+    xs = ((np.arange(grid) + 0.5) * spec.X / grid).astype(np.int64)
+    ys = ((np.arange(grid) + 0.5) * spec.Y / grid).astype(np.int64)
+    pts = []
+    for x in xs:
+        for y in ys:
+            h = spec.centre + spec.amp * math.sin(2.0 * math.pi * x / spec.px) * math.cos(2.0 * math.pi * y / spec.py)
+            pts.append((int(x), int(y), min(max(int(math.floor(h + 0.5)), 0), spec.Z - 1)))
+    return np.array(pts, dtype=np.int32)
+
+
+BAND_STICK = 16       # rows above and below the center surface, before the band factor
+BAND_FACTOR = 2       # narrow-band factor: half = 32, 65 rows per column
+BAND_OUTSIDE = 1200   # cost of band rows outside the image (the costs' cap)
