@@ -338,7 +338,9 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
                 if (i < n) {
                     const int uv = cur[i];
                     const int vi = SINGLE ? 0 : find_volume(sbase, b.nvol, uv);
-                    const Grid g = SINGLE ? g0 : b.vols[vi];
+                    // the volume's view read where used (a reference into the table),
+                    // not copied whole into registers for every frontier node
+                    const Grid &g = SINGLE ? g0 : b.vols[vi];
                     base = sbase[vi];
                     const int v = uv - base;
                     int x, y, z;
