@@ -123,6 +123,13 @@ __device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int z,
         : "memory");
 }
 
+// Asynchronous copy of one 4-byte word from global to shared memory (through L1: every
+// word a tile reads can only have grown since an older copy of its line was cached, so a
+// stale read makes a push smaller, never invalid).
+__device__ __forceinline__ void cp_async4(int *dst, const int32_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 // Wait for phase `parity` of an mbarrier, with an iteration limit; false if it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     const unsigned a = smem_u32(bar);
@@ -222,24 +229,42 @@ __device__ __forceinline__ bool tile_visit(const Grid &g, const Batch &b, int ti
             }
         }
     } else {
+        // word by word, as asynchronous 4-byte copies (no register staging, all in flight
+        // together); a slot outside the graph gets its values by plain stores
 #pragma unroll
         for (int k = 0; k < kPerThread; ++k) {
             const int s = threadIdx.x + kTileThreads * k;
             bool own;
             const int u = node_of(s, own);
-            S.lab[s] = own ? ldcg(g.lab + u) : POG_INF;
-            const int e = own ? ldcg(g.exc + u) : 0;
-            if (e < 0) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes
-            S.exc[s] = e;
-            S.snk[s] = own ? ldcg(g.snk + u) : 0;
-            S.fdn[s] = own ? ldcg(g.fdn + u) : 0;
+            if (own) {
+                cp_async4(S.lab + s, g.lab + u);
+                cp_async4(S.exc + s, g.exc + u);
+                cp_async4(S.snk + s, g.snk + u);
+                cp_async4(S.fdn + s, g.fdn + u);
 #pragma unroll
-            for (int d = 0; d < 4; ++d) S.fh[d][s] = own ? ldcg(g.fh[d] + u) : 0;
-            if (soft) {
+                for (int d = 0; d < 4; ++d) cp_async4(S.fh[d] + s, g.fh[d] + u);
+                if (soft) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j) SS.gs[j][s] = own ? ldcg(g.gs[j] + u) : 0;
+                    for (int j = 0; j < 2; ++j) cp_async4(SS.gs[j] + s, g.gs[j] + u);
+                }
+            } else {
+                S.lab[s] = POG_INF;
+                S.exc[s] = 0;
+                S.snk[s] = 0;
+                S.fdn[s] = 0;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) S.fh[d][s] = 0;
+                if (soft) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) SS.gs[j][s] = 0;
+                }
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k)
+            if (S.exc[threadIdx.x + kTileThreads * k] < 0)
+                atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);  // wrapped by small pushes
     }
     __syncthreads();
 
@@ -435,10 +460,23 @@ __device__ __forceinline__ bool tile_visit(const Grid &g, const Batch &b, int ti
         still |= own && S.exc[s] > 0 && S.lab[s] < POG_INF;
     }
     const unsigned keep = __syncthreads_or(still) ? 1u << 13 : 0u;  // bit 13, (dx, dy, dz) = 0: this tile
-    if (threadIdx.x < 27 && (((nbmask | keep) >> threadIdx.x) & 1u)) {
+    if (threadIdx.x < 32) {
+        // warp 0 lists the tiles of the 27-bit mask: each lane claims its tile's flag, and
+        // the winners take their list slots with one atomic on the sweep's shared counter
+        // (one per visit instead of one per listed tile: that counter is contended)
         const int t = threadIdx.x;
-        const int nx = txy / nty + t / 9 - 1, ny = txy % nty + (t / 3) % 3 - 1, nz = tz + t % 3 - 1;
-        list_tile(tile - local_tile + (nx * nty + ny) * ntz + nz, L.nflag, L.nlist, L.ncount);
+        int ut = -1;
+        bool won = false;
+        if (t < 27 && (((nbmask | keep) >> t) & 1u)) {
+            const int nx = txy / nty + t / 9 - 1, ny = txy % nty + (t / 3) % 3 - 1, nz = tz + t % 3 - 1;
+            ut = tile - local_tile + (nx * nty + ny) * ntz + nz;
+            won = !__ldcg(L.nflag + ut) && atomicExch(L.nflag + ut, 1) == 0;
+        }
+        const unsigned winners = __ballot_sync(0xffffffffu, won);
+        int slot = 0;
+        if (t == 0 && winners) slot = atomicAdd(L.ncount, __popc(winners));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (won) L.nlist[slot + __popc(winners & ((1u << t) - 1u))] = ut;
     }
     if (threadIdx.x == 0) atomicAdd(&b.ctr->tiles_visited, 1ull);
 
