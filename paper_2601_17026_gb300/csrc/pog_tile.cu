@@ -381,8 +381,12 @@ __device__ __forceinline__ bool tile_visit(const Grid &g, const Batch &b, int ti
                     bres = res[a];
                 }
             if (bk < 0 || h <= best) {  // relabel (Algorithm 2)
-                S.lab[s] = best >= POG_INF - 1 ? POG_INF : best + 1;
-                continue;
+                const int nh = best >= POG_INF - 1 ? POG_INF : best + 1;
+                S.lab[s] = nh;
+                // the lowest residual arc found by this gather is admissible at the new
+                // label (nh = its far end's label + 1): push along it in the same step
+                // instead of gathering the neighbourhood again in the next local sweep
+                if (nh >= POG_INF) continue;
             }
             // push along arc bk (Algorithm 2)
             const int bd = bk >= 2 ? (bk - 2) / 3 : 0;
