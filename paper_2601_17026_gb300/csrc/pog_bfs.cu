@@ -371,11 +371,18 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
     for (int vi = 0; vi < b.nvol; ++vi) {
         const Grid g = SINGLE ? g0 : b.vols[vi];
         unsigned long long active = 0;
-        for (int u = tid; u < g.N; u += stride) {
-            if (u % g.Z == 0) continue;
-            const int e = g.exc[u];
-            if (e < 0) atomicOr(err, POG_ERR_FLOW_RANGE);  // a wrapped excess
-            if (e > 0 && g.lab[u] < POG_INF) ++active;
+        for (int u0 = tid; u0 < g.N; u0 += 4 * stride) {  // four independent excess loads in flight
+            int e[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = u0 + j * stride;
+                e[j] = (u < g.N && u % g.Z != 0) ? __ldcg(g.exc + u) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (e[j] < 0) atomicOr(err, POG_ERR_FLOW_RANGE);  // a wrapped excess
+                if (e[j] > 0 && __ldcg(g.lab + u0 + j * stride) < POG_INF) ++active;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(0xffffffffu, active, o);
