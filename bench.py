@@ -157,7 +157,13 @@ def algorithmic_bytes(N, alpha, tiles_per_sweep, scans_per_sweep):
 # of one launch divided by the launch's units: tile visits for the tiled sweep, nodes
 # for the global relabel), with the SHA-256 prefix of the kernel source they were taken
 # on. A kernel whose source changed since reports no traffic.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # 64 launches after the first global relabel (warm L2, --cache-control none): 18.44 GB over
+    # 290,567 tile visits
+    "k_tile_push_relabel": {"bytes_per_unit": 63479, "unit": "tile visit", "source_sha": "80e2f306e500ec0b"},
+    # the global relabel after those 64 sweeps: 4.29 GB over 25,165,824 nodes
+    "k_global_relabel": {"bytes_per_unit": 170.4, "unit": "node", "source_sha": "5c292e869db59222"},
+}
 
 
 def _source_sha(kernel):
