@@ -115,7 +115,9 @@ def test_options_do_not_change_results():
                 dict(flags=pog.POG_FLAG_NO_GAP), dict(tile_sweeps=16), dict(flags=pog.POG_FLAG_NODE_SWEEPS),
                 dict(flags=pog.POG_FLAG_NO_PREPUSH), dict(bfs_blocks_per_sm=1), dict(tile_sweeps=64),
                 dict(tile_shape=1), dict(tile_shape=2), dict(tile_shape=3), dict(bfs_bottom_up_ratio=-1),
-                dict(bfs_bottom_up_ratio=1), dict(relabel_factor=0.25), dict(sweeps_per_relabel=3, tile_shape=3)]:
+                dict(bfs_bottom_up_ratio=1), dict(relabel_factor=0.25), dict(sweeps_per_relabel=3, tile_shape=3),
+                dict(flags=pog.POG_FLAG_NO_TMA), dict(flags=pog.POG_FLAG_NO_TMA, tile_shape=1),
+                dict(relabel_factor=3.0, tile_shape=1, bfs_bottom_up_ratio=-1)]:
         flow, h = gpu_solve(cost, 2, 10, **opt)
         assert flow == ref.flow
         np.testing.assert_array_equal(h, ref.heights)
