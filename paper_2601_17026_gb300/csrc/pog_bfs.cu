@@ -56,10 +56,15 @@ __device__ __forceinline__ bool grid_sync(BfsSync *s, unsigned nblocks, int *err
     return ok;
 }
 
-// Append up to kMaxArcs nodes per lane (slot k of `hd.node` when bit k of `mask`) with
-// one atomic per warp; every lane of the warp must call it.
-__device__ __forceinline__ void warp_append_mask(unsigned mask, const Hood &hd, int *queue, int *size) {
-    const int lane = threadIdx.x & 31;
+// Append up to kMaxArcs nodes per thread (slot k of `hd.node` when bit k of `mask`) with one
+// atomic per block: a frontier's size counter is shared by every block, and same-address
+// atomics serialise, so one per warp made large levels wait on the counter. Every thread of
+// the block must call it (the call holds two block barriers).
+template <int K>
+__device__ __forceinline__ void block_append_mask(unsigned mask, const int (&node)[K], int *queue, int *size) {
+    __shared__ int warp_off[32];
+    __shared__ int block_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cnt = __popc(mask);
     int incl = cnt;
 #pragma unroll
@@ -67,14 +72,22 @@ __device__ __forceinline__ void warp_append_mask(unsigned mask, const Hood &hd, 
         const int t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    int base = 0;
-    if (lane == 31) base = atomicAdd(size, total);
-    base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+    if (lane == 31) warp_off[warp] = incl;  // the warp's total
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int t = warp_off[w];
+            warp_off[w] = sum;
+            sum += t;
+        }
+        block_base = sum ? atomicAdd(size, sum) : 0;
+    }
+    __syncthreads();
+    int at = block_base + warp_off[warp] + incl - cnt;
 #pragma unroll
-    for (int k = 0; k < kMaxArcs; ++k)
-        if (mask & (1u << k)) queue[base++] = hd.node[k];
+    for (int k = 0; k < K; ++k)
+        if (mask & (1u << k)) queue[at++] = node[k];
 }
 
 // Append `u` to a queue; the lanes that append together share one atomic.
@@ -249,7 +262,8 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
         const Grid g = SINGLE ? g0 : b.vols[v];
         const int base = sbase[v];
         unvisited += (long long)g.N - (long long)g.X * g.Y;  // nodes z >= 1
-        for (int u0 = tid - lane; u0 < g.N; u0 += stride) {
+        for (int ub = blockIdx.x * blockDim.x; ub < g.N; ub += stride) {  // block-uniform trip count
+            const int u0 = ub + (threadIdx.x & ~31);
             const int u = u0 + lane;
             int l = POG_INF;
             bool bottom = false;
@@ -272,9 +286,10 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
                 g.lab[u] = l;
             }
             const unsigned seen = __ballot_sync(0xffffffffu, bottom || l < POG_INF);
-            if (lane == 0) visit[(base + u0) >> 5] = seen;
+            if (lane == 0 && u0 < g.N) visit[(base + u0) >> 5] = seen;
             ones += l == 1;
-            if (l == 2) warp_append(base + u, qb, &s->size[2]);
+            const int un[1] = {base + u};
+            block_append_mask(l == 2 ? 1u : 0u, un, qb, &s->size[2]);
         }
     }
 #pragma unroll
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_global_rel
                         hd.node[k] += base;  // to union indices
                     }
                 }
-                warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
+                block_append_mask(won, hd.node, nxt, &s->size[(level + 1) % 3]);
             }
         }
         if (!grid_sync(s, nblocks, err, b.wait_limit)) return;
@@ -446,7 +461,7 @@ __global__ void __launch_bounds__(THREADS, kBfsSmThreads / THREADS) k_cut_reach(
                     hd.node[k] += base;
                 }
             }
-            warp_append_mask(won, hd, nxt, &s->size[(level + 1) % 3]);
+            block_append_mask(won, hd.node, nxt, &s->size[(level + 1) % 3]);
         }
         if (!grid_sync(s, nblocks, err, b.wait_limit)) return;
         int *t = cur;
