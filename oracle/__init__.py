@@ -54,6 +54,12 @@ def _configure(lib):
     lib.oracle_solve.restype = ctypes.c_int
     lib.oracle_solve.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                  ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, i64p, i32p, i64p]
+    lib.oracle_solve_convex.restype = ctypes.c_int
+    lib.oracle_solve_convex.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, i64p, ctypes.c_int32, i64p, i32p, i64p]
+    lib.oracle_energy_convex.restype = ctypes.c_int64
+    lib.oracle_energy_convex.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, i64p, i32p, i32p]
     lib.oracle_energy.restype = ctypes.c_int64
     lib.oracle_energy.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_int64, i32p, i32p]
@@ -120,6 +126,45 @@ def solve(cost, delta: int, alpha: int, check: bool = False, lib=None) -> Oracle
     if rc != 0:
         raise RuntimeError(f"oracle_solve failed: {ERRORS.get(rc, rc)}")
     return OracleResult(int(flow.value), heights, *[int(v) for v in stats])
+
+
+def _profile(delta: int, f) -> np.ndarray:
+    fa = np.ascontiguousarray(np.asarray(f if f is not None else [], dtype=np.int64).reshape(-1))
+    if fa.size != delta:
+        raise ValueError("f must hold f(1..delta)")
+    return fa
+
+
+def solve_convex(cost, delta: int, f, check: bool = False, lib=None) -> OracleResult:
+    """Max-flow value and minimal-cut surface with the convex pairwise cost f
+    (f[d-1] = f(d) for d = 1..delta, f(0) = 0): the literal graph with one layer of soft
+    arcs per height drop d < delta, capacity the second difference of f (Section 1.2's
+    convex edge costs over an edge interval), solved by the same Dinic."""
+    lib = lib or _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    fa = _profile(delta, f)
+    heights = np.empty((X, Y), dtype=np.int32)
+    flow = ctypes.c_int64(0)
+    stats = (ctypes.c_int64 * 4)()
+    rc = lib.oracle_solve_convex(_i32(c), X, Y, Z, int(delta), fa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 1 if check else 0, ctypes.byref(flow), _i32(heights), stats)
+    if rc != 0:
+        raise RuntimeError(f"oracle_solve_convex failed: {ERRORS.get(rc, rc)}")
+    return OracleResult(int(flow.value), heights, *[int(v) for v in stats])
+
+
+def energy_convex(cost, heights, delta: int, f):
+    """(E, feasible): sum_col c(col, h) + sum over unordered 4-neighbour pairs f(|h_p - h_q|)."""
+    lib = _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    fa = _profile(delta, f)
+    h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
+    feas = ctypes.c_int32(0)
+    e = lib.oracle_energy_convex(_i32(c), X, Y, Z, int(delta), fa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 _i32(h), ctypes.byref(feas))
+    return int(e), bool(feas.value)
 
 
 def solve_state(cost, delta: int, alpha: int, lib=None):

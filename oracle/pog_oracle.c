@@ -24,6 +24,17 @@
  *                                                           in-grid 4-neighbour)
  *   (x,y,z) -> (x',y',z), capacity alpha, if alpha > 0     (soft smoothness: one arc
  *                                                           per ordered neighbour pair)
+ *
+ * General convex pairwise cost (the convex edge costs of an edge interval, Section 1.2):
+ * E_prior = sum over unordered 4-neighbour pairs of f(|h_p - h_q|), f(0) = 0, f convex
+ * on 0..delta. It is the sum of layers d = 0..delta-1 of soft arcs
+ *   (x,y,z) -> (x',y',z-d), capacity k_d, for z - d >= 0,
+ * with k_0 = f(1) and k_d = f(d+1) - 2 f(d) + f(d-1) (the second difference of f): the
+ * layer-d arcs from column p to column q that a surface cuts are those with
+ * h_q + d < z <= h_p, (h_p - h_q - d)^+ of them, and sum_d k_d (t - d)^+ = f(t) for
+ * 0 <= t <= delta. The linear penalty alpha |h_p - h_q| is the single layer k_0 = alpha.
+ * An arc whose head would lie below z = 0 is never cut (that node is in every closed
+ * set) and is left out.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -91,8 +102,9 @@ static void add_arc(orc_graph *g, int mode, int64_t u, int64_t v, int64_t c) {
     }
 }
 
+/* Soft layers: kcap[d] is the capacity of the arcs that drop d heights, d < nk. */
 static void enumerate_arcs(orc_graph *g, int mode, const int32_t *c, int32_t X, int32_t Y,
-                           int32_t Z, int32_t delta, int64_t alpha) {
+                           int32_t Z, int32_t delta, const int64_t *kcap, int32_t nk) {
     const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
     const int64_t bsum = bottom_layer_sum(c, X, Y, Z);
     for (int64_t x = 0; x < X; ++x)
@@ -108,7 +120,8 @@ static void enumerate_arcs(orc_graph *g, int mode, const int32_t *c, int32_t X, 
                     if (xq < 0 || xq >= X || yq < 0 || yq >= Y) continue;
                     const int64_t zq = (z - delta > 0) ? z - delta : 0;
                     add_arc(g, mode, v, idx3(Y, Z, xq, yq, zq), ORC_INF);
-                    if (alpha > 0) add_arc(g, mode, v, idx3(Y, Z, xq, yq, z), alpha);
+                    for (int64_t l = 0; l < nk; ++l)
+                        if (kcap[l] > 0 && z - l >= 0) add_arc(g, mode, v, idx3(Y, Z, xq, yq, z - l), kcap[l]);
                 }
             }
 }
@@ -124,13 +137,13 @@ static void graph_free(orc_graph *g) {
 }
 
 static int graph_build(orc_graph *g, const int32_t *c, int32_t X, int32_t Y, int32_t Z,
-                       int32_t delta, int64_t alpha, int keep_cap0) {
+                       int32_t delta, const int64_t *kcap, int32_t nk, int keep_cap0) {
     memset(g, 0, sizeof *g);
     const int64_t N = (int64_t)X * Y * Z;
     g->n = N + 2;
     g->first = calloc((size_t)g->n + 1, sizeof(int64_t));
     if (!g->first) return ORC_E_NOMEM;
-    enumerate_arcs(g, 0, c, X, Y, Z, delta, alpha);
+    enumerate_arcs(g, 0, c, X, Y, Z, delta, kcap, nk);
     for (int64_t i = 0; i < g->n; ++i) g->first[i + 1] += g->first[i];
     g->m = g->first[g->n];
     g->head = malloc((size_t)g->m * sizeof(int32_t));
@@ -143,7 +156,7 @@ static int graph_build(orc_graph *g, const int32_t *c, int32_t X, int32_t Y, int
         return ORC_E_NOMEM;
     }
     memcpy(g->fill, g->first, (size_t)g->n * sizeof(int64_t));
-    enumerate_arcs(g, 1, c, X, Y, Z, delta, alpha);
+    enumerate_arcs(g, 1, c, X, Y, Z, delta, kcap, nk);
     free(g->fill);
     g->fill = NULL;
     return ORC_OK;
@@ -274,14 +287,12 @@ static int check_invariants(const orc_graph *g, int64_t s, int64_t t, const uint
  * half-arcs. check != 0 keeps the initial capacities and verifies Eq. 2-4 and
  * Theorem 1.1 on the result.
  */
-int oracle_solve(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
-                 int64_t alpha, int32_t check, int64_t *flow_out, int32_t *heights_out,
-                 int64_t *stats_out) {
-    if (!cost || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 || !flow_out || !heights_out)
-        return ORC_E_ARGS;
+static int solve_layers(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                        const int64_t *kcap, int32_t nk, int32_t check, int64_t *flow_out,
+                        int32_t *heights_out, int64_t *stats_out) {
     if ((int64_t)X * Y * Z + 2 > INT32_MAX) return ORC_E_ARGS;
     orc_graph g;
-    int rc = graph_build(&g, cost, X, Y, Z, delta, alpha, check != 0);
+    int rc = graph_build(&g, cost, X, Y, Z, delta, kcap, nk, check != 0);
     if (rc != ORC_OK) return rc;
     const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
     orc_dinic d = {0};
@@ -325,6 +336,75 @@ done:
     return rc;
 }
 
+int oracle_solve(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                 int64_t alpha, int32_t check, int64_t *flow_out, int32_t *heights_out,
+                 int64_t *stats_out) {
+    if (!cost || X < 1 || Y < 1 || Z < 1 || delta < 0 || alpha < 0 || !flow_out || !heights_out)
+        return ORC_E_ARGS;
+    return solve_layers(cost, X, Y, Z, delta, &alpha, 1, check, flow_out, heights_out, stats_out);
+}
+
+/* Layer capacities k_0 = f(1), k_d = f(d+1) - 2 f(d) + f(d-1) of a convex pairwise cost
+ * given as f[0..delta-1] = f(1..delta) (f(0) = 0). Returns 0 when f is not convex or
+ * f(1) < 0. */
+static int convex_layers(const int64_t *f, int32_t delta, int64_t *kcap) {
+    for (int32_t d = 0; d < delta; ++d) {
+        const int64_t fd = d == 0 ? 0 : f[d - 1];
+        const int64_t fm = d <= 1 ? 0 : f[d - 2];
+        kcap[d] = d == 0 ? f[0] : f[d] - 2 * fd + fm;
+        if (kcap[d] < 0) return 0;
+    }
+    return 1;
+}
+
+/*
+ * Solve one volume with the convex pairwise cost f (f[0..delta-1] = f(1..delta), f(0) = 0):
+ * minimise sum_col c(col, h(col)) + sum over unordered 4-neighbour pairs f(|h_p - h_q|)
+ * subject to |h_p - h_q| <= delta. Outputs as oracle_solve. ORC_E_ARGS when f is not
+ * convex (a negative second difference, or f(1) < 0).
+ */
+int oracle_solve_convex(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                        const int64_t *f, int32_t check, int64_t *flow_out, int32_t *heights_out,
+                        int64_t *stats_out) {
+    if (!cost || X < 1 || Y < 1 || Z < 1 || delta < 0 || (delta > 0 && !f) || !flow_out || !heights_out)
+        return ORC_E_ARGS;
+    int64_t *kcap = malloc(((size_t)delta + 1) * sizeof(int64_t));
+    if (!kcap) return ORC_E_NOMEM;
+    int rc = convex_layers(f, delta, kcap)
+                 ? solve_layers(cost, X, Y, Z, delta, kcap, delta, check, flow_out, heights_out, stats_out)
+                 : ORC_E_ARGS;
+    free(kcap);
+    return rc;
+}
+
+/*
+ * Surface energy with the convex pairwise cost, from its definition:
+ * E = sum_col c(col, h(col)) + sum over unordered 4-neighbour pairs f(|h_p - h_q|).
+ * *feasible is set to 0 if some pair differs by more than delta or a height is outside
+ * [0, Z) (those pairs add nothing).
+ */
+int64_t oracle_energy_convex(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                             const int64_t *f, const int32_t *h, int32_t *feasible) {
+    int64_t e = 0;
+    int ok = 1;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y) {
+            const int64_t hp = h[x * Y + y];
+            if (hp < 0 || hp >= Z) { ok = 0; continue; }
+            e += cost[idx3(Y, Z, x, y, hp)];
+            for (int k = 0; k < 2; ++k) {
+                const int64_t xq = x + (k == 0), yq = y + (k == 1);
+                if (xq >= X || yq >= Y) continue;
+                const int64_t dq = hp - h[xq * Y + yq];
+                const int64_t ad = dq < 0 ? -dq : dq;
+                if (ad > delta) { ok = 0; continue; }
+                if (ad > 0) e += f[ad - 1];
+            }
+        }
+    if (feasible) *feasible = ok;
+    return e;
+}
+
 /*
  * Solve one volume as oracle_solve does and describe the final flow in the layout of a
  * solver state (the arrays oracle_certify takes, include/pog.h's export), so that the
@@ -348,7 +428,7 @@ int oracle_solve_state(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int
         return ORC_E_ARGS;
     if ((int64_t)X * Y * Z + 2 > INT32_MAX) return ORC_E_ARGS;
     orc_graph g;
-    int rc = graph_build(&g, cost, X, Y, Z, delta, alpha, 1);
+    int rc = graph_build(&g, cost, X, Y, Z, delta, &alpha, 1, 1);
     if (rc != ORC_OK) return rc;
     const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
     orc_dinic d = {0};

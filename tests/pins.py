@@ -117,3 +117,84 @@ def identity_offset(cost: np.ndarray) -> int:
     """
     w = node_weights(cost)
     return int(-1 - int(cost[:, :, 0].astype(np.int64).sum()) + int(-w[w < 0].sum()))
+
+
+# --------------------------------------------------------------------------------------
+# Convex pairwise costs: E(h) = sum_col c(col, h(col)) + sum over unordered 4-neighbour
+# pairs f(|h_p - h_q|), |h_p - h_q| <= delta. `fv` holds f(0..delta) (fv[0] = 0).
+# --------------------------------------------------------------------------------------
+
+def energy_pairwise(cost: np.ndarray, h: np.ndarray, fv) -> int:
+    X, Y, _ = cost.shape
+    h = np.asarray(h, dtype=np.int64).reshape(X, Y)
+    fv = np.asarray(fv, dtype=np.int64)
+    e = int(np.take_along_axis(cost.astype(np.int64), h[:, :, None], axis=2).sum())
+    e += int(fv[np.abs(np.diff(h, axis=0))].sum() + fv[np.abs(np.diff(h, axis=1))].sum())
+    return e
+
+
+def brute_force_pairwise(cost: np.ndarray, delta: int, fv):
+    """(E_min, h_min, optimal surfaces) over all Z^(X*Y) surfaces, pairwise cost table fv."""
+    X, Y, Z = cost.shape
+    n = X * Y
+    assert Z ** n <= 200_000, "volume too large for enumeration"
+    fv = np.asarray(fv, dtype=np.int64)
+    hs = np.array(list(itertools.product(range(Z), repeat=n)), dtype=np.int64).reshape(-1, X, Y)
+    ok = np.ones(len(hs), dtype=bool)
+    if X > 1:
+        ok &= np.all(np.abs(np.diff(hs, axis=1)) <= delta, axis=(1, 2))
+    if Y > 1:
+        ok &= np.all(np.abs(np.diff(hs, axis=2)) <= delta, axis=(1, 2))
+    hs = hs[ok]
+    c = cost.astype(np.int64)
+    cols = np.arange(n)
+    e = c.reshape(n, Z)[cols[None, :], hs.reshape(len(hs), n)].sum(axis=1)
+    if X > 1:
+        e = e + fv[np.abs(np.diff(hs, axis=1))].sum(axis=(1, 2))
+    if Y > 1:
+        e = e + fv[np.abs(np.diff(hs, axis=2))].sum(axis=(1, 2))
+    emin = int(e.min())
+    opt = hs[e == emin]
+    return emin, opt.min(axis=0), opt
+
+
+def row_dp_pairwise(cost: np.ndarray, delta: int, fv):
+    """(E_min, h_min) for one row of columns with pairwise cost table fv, by the forward /
+    backward recursion of ``row_dp`` with f(|h - h'|) in place of alpha |h - h'|."""
+    X, Y, Z = cost.shape
+    assert X == 1 or Y == 1
+    c = cost.reshape(-1, Z).astype(np.int64)
+    L = c.shape[0]
+    hh = np.arange(Z)
+    dist = np.abs(hh[:, None] - hh[None, :])
+    big = np.int64(1) << 60
+    fv = np.asarray(fv, dtype=np.int64)
+    trans = np.where(dist <= delta, fv[np.minimum(dist, delta)], big)
+
+    def sweep(rows):
+        out = np.empty_like(rows)
+        out[0] = rows[0]
+        for i in range(1, len(rows)):
+            out[i] = rows[i] + np.min(out[i - 1][None, :] + trans, axis=1)
+        return out
+
+    A = sweep(c)
+    B = sweep(c[::-1])[::-1]
+    emin = int(A[-1].min())
+    total = A + B - c
+    h = np.array([int(np.flatnonzero(total[i] == emin)[0]) for i in range(L)], dtype=np.int64)
+    return emin, h.reshape(X, Y)
+
+
+def convex_profiles(delta: int):
+    """A few convex f(1..delta) (f(0) = 0) of different shapes: linear, quadratic,
+    truncated-linear-then-steep, zero, and a single kink."""
+    t = np.arange(1, delta + 1, dtype=np.int64)
+    out = {
+        "linear3": 3 * t,
+        "quadratic": 2 * t * t,
+        "hinge": np.maximum(0, t - 1) * 7,
+        "zero": 0 * t,
+        "quad_plus_linear": t * t + 5 * t,
+    }
+    return {k: v for k, v in out.items()}

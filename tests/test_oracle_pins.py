@@ -138,7 +138,8 @@ MUTANTS = {
     "hard arc off by one": ("const int64_t zq = (z - delta > 0) ? z - delta : 0;",
                             "const int64_t zq = (z - delta - 1 > 0) ? z - delta - 1 : 0;"),
     "x/y transposed": ("return (x * Y + y) * Z + z;", "return (y * Y + x) * Z + z;"),
-    "soft arcs dropped": ("if (alpha > 0) add_arc(g, mode, v, idx3(Y, Z, xq, yq, z), alpha);", ";"),
+    "soft arcs dropped": ("if (kcap[l] > 0 && z - l >= 0) add_arc(g, mode, v, idx3(Y, Z, xq, yq, z - l), kcap[l]);",
+                          ";"),
     "down arc dropped": ("if (z >= 1) add_arc(g, mode, v, idx3(Y, Z, x, y, z - 1), ORC_INF);", ";"),
     "weight difference reversed": ("(int64_t)c[idx3(Y, Z, x, y, z)] - (int64_t)c[idx3(Y, Z, x, y, z - 1)]",
                                    "(int64_t)c[idx3(Y, Z, x, y, z - 1)] - (int64_t)c[idx3(Y, Z, x, y, z)]"),
