@@ -381,6 +381,41 @@ POG_API pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int32_t
                                      int32_t alpha, const pog_options *opt, void *stream, int64_t *flow_out,
                                      int32_t *heights_dev);
 
+/*
+ * Convex pairwise costs: the general optimal VCE-weight net surface of Section 1.2, whose
+ * proper-order graph joins every vertex to an interval of vertices of each adjacent
+ * column, with convex costs over that edge interval. Minimises
+ *     E(h) = sum_col c(col, h(col)) + sum_{4-neighbour pairs} f(|h_p - h_q|)
+ * subject to |h_p - h_q| <= delta, for a convex f with f(0) = 0. The graph carries, besides
+ * the column and hard arcs of pog_build, one layer of soft arcs (x,y,z) -> (x',y',z-d) per
+ * height drop d = 0 .. delta-1, of capacity k_0 = f(1) and k_d = f(d+1) - 2 f(d) + f(d-1):
+ * a surface cuts (h_p - h_q - d)^+ arcs of layer d from column p to column q, and
+ * sum_d k_d (t - d)^+ = f(t). pog_build's alpha is the profile f(t) = alpha * t (layer 0
+ * only). Solved on the device by push-relabel with global relabelling and the minimal
+ * cut's reach, every arc addressed from (x, y, z) as in pog_build.
+ *   cost_dev    : device, int32 [X][Y][Z], |c| < 2^30 (else POG_E_OVERFLOW).
+ *   X, Y, Z     : >= 1, X*Y*Z < 2^31.
+ *   delta       : 0 <= delta <= POG_CONVEX_MAX_DELTA.
+ *   f_host      : host, int64 [delta]: f(1), ..., f(delta) (may be NULL when delta = 0).
+ *                 POG_E_INVALID unless 0 <= k_d < 2^30 for every d (f convex, f(1) >= 0).
+ *   opt         : host, may be NULL. Used: sweeps_per_relabel (default 32), max_rounds,
+ *                 flags (POG_FLAG_TIMING), test_fail_alloc (1: the state allocation fails).
+ *   stream      : cudaStream_t for all device work.
+ *   flow_out    : host, receives the max-flow value of the literal s-t graph.
+ *   energy_out  : host, may be NULL: receives E*(h) = max-flow - K (K as for pog_energy).
+ *   heights_dev : device, int32 [X][Y]: the surface of the minimal minimum cut.
+ *   stats_out   : host, may be NULL: counters of this solve (pog_stats_t); this path has no
+ *                 tiles, and its tiles_visited field counts the active nodes listed for the
+ *                 push/relabel sweeps, summed over the sweeps.
+ * Allocates (10 + 4 L) * 4 + 12 bytes per node on the device (L = layers d >= 1 with
+ * k_d > 0) and frees them before returning; blocks until the work on `stream` is done.
+ */
+#define POG_CONVEX_MAX_DELTA 32
+POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                                    const int64_t *f_host, const pog_options *opt, void *stream,
+                                    int64_t *flow_out, int64_t *energy_out, int32_t *heights_dev,
+                                    pog_stats_t *stats_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpog.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["pog_api.cu", "pog_kernels.cu", "pog_bfs.cu", "pog_tile.cu", "pog_noalloc.cu", "pog_band.cu"]
+SOURCES = ["pog_api.cu", "pog_kernels.cu", "pog_bfs.cu", "pog_tile.cu", "pog_noalloc.cu", "pog_band.cu", "pog_convex.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

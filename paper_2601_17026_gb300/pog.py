@@ -30,11 +30,12 @@ POG_FLAG_NO_PREPUSH = 4
 POG_FLAG_NODE_SWEEPS = 8
 POG_FLAG_NO_TMA = 16
 POG_FLAG_COLD_HINGE = 32
+POG_CONVEX_MAX_DELTA = 32
 
 EXPORTED = ["pog_build", "pog_build_f32", "pog_build_f32_augmented", "pog_maxflow", "pog_surface", "pog_energy",
             "pog_stats", "pog_export_state", "pog_trace", "pog_free", "pog_strerror", "pog_quantise", "pog_backward",
             "pog_surface_energy", "pog_solve_batch", "pog_solve_batch_f32", "pog_solve_batch_f32_hinge",
-            "pog_narrow_band", "pog_band_heights", "pog_solve_noalloc"]
+            "pog_narrow_band", "pog_band_heights", "pog_solve_noalloc", "pog_solve_convex"]
 
 
 class PogError(RuntimeError):
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH):
                                           i64p, i64p, vp, vp],
             "pog_narrow_band": [vp, i32, i32, i32, vp, i32, i32, i32, i32, vp, vp, vp],
             "pog_band_heights": [vp, vp, i32, i32, i32, vp, vp],
+            "pog_solve_convex": [vp, i32, i32, i32, i32, vp, opts, vp, i64p, i64p, vp, ctypes.POINTER(pog_stats_t)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -428,6 +430,32 @@ def pog_solve_noalloc(cost, delta: int, alpha: int, heights, options: pog_option
                                     ctypes.byref(options) if options else None, _stream(stream), ctypes.byref(flow),
                                     _dev(heights, torch.int32, "heights")), "pog_solve_noalloc")
     return int(flow.value)
+
+
+def pog_solve_convex(cost, delta: int, f, heights=None, options: pog_options | None = None, stream=None):
+    """Solve with the convex pairwise cost f (f[d-1] = f(d), d = 1..delta, f(0) = 0).
+    Returns (flow, energy, heights, stats): the max-flow value, E*(h), the int32 CUDA
+    tensor [X, Y] of the minimal cut's surface and the solve's counters (dict)."""
+    import torch
+
+    if not isinstance(cost, torch.Tensor) or cost.dim() != 3:
+        raise PogError(POG_E_INVALID, "cost must be a CUDA tensor [X, Y, Z]")
+    X, Y, Z = cost.shape
+    fa = np.ascontiguousarray(np.asarray(f if f is not None else [], dtype=np.int64).reshape(-1))
+    if fa.size != int(delta):
+        raise PogError(POG_E_INVALID, "f must hold f(1..delta)")
+    if heights is None:
+        heights = torch.empty((X, Y), dtype=torch.int32, device=cost.device)
+    elif (not isinstance(heights, torch.Tensor) or tuple(heights.shape) != (X, Y)
+            or heights.device != cost.device):
+        raise PogError(POG_E_INVALID, "heights must be an int32 tensor [X, Y] on the device of cost")
+    flow, energy, st = ctypes.c_int64(0), ctypes.c_int64(0), pog_stats_t()
+    fptr = ctypes.c_void_p(fa.ctypes.data) if fa.size else None
+    _check(load().pog_solve_convex(_dev(cost, torch.int32, "cost"), X, Y, Z, int(delta), fptr,
+                                   ctypes.byref(options) if options else None, _stream(stream), ctypes.byref(flow),
+                                   ctypes.byref(energy), _dev(heights, torch.int32, "heights"), ctypes.byref(st)),
+           "pog_solve_convex")
+    return int(flow.value), int(energy.value), heights, {n: getattr(st, n) for n, _ in pog_stats_t._fields_}
 
 
 def solve(cost, delta: int, alpha: int, options: pog_options | None = None, stream=None):

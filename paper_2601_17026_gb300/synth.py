@@ -287,3 +287,25 @@ def horizon_landmarks(spec: HorizonSpec, grid: int = 8) -> np.ndarray:
 BAND_STICK = 16       # rows above and below the center surface, before the band factor
 BAND_FACTOR = 2       # narrow-band factor: half = 32, 65 rows per column
 BAND_OUTSIDE = 1200   # cost of band rows outside the image (the costs' cap)
+
+
+# ---------------------------------------------------------------------------------------
+# Convex pairwise costs (the general proper-order graph): an edge interval of 10 vertices
+# per adjacent column (height drops d = 0..9, delta = 9) with a quadratic cost f(t) = 4 t^2
+# on the layered-horizon volumes (medium formula scaled to the volume's z extent).
+# ---------------------------------------------------------------------------------------
+
+CONVEX_DELTA = 9
+CONVEX_QUAD = 4
+CONVEX_SHAPE = (256, 256, 128)
+
+
+def convex_profile(delta: int = CONVEX_DELTA, a: int = CONVEX_QUAD) -> np.ndarray:
+    """int64 f(1..delta) of f(t) = a t^2."""
+    t = np.arange(1, delta + 1, dtype=np.int64)
+    return a * t * t
+
+
+def convex_cost(X: int, Y: int, Z: int, seed: int = BASE_SEED) -> np.ndarray:
+    """int32 [X, Y, Z] layered-horizon volume of the convex workload (stream 5)."""
+    return horizon_cost(scaled_spec(X, Y, Z, seed, 5))

@@ -4,6 +4,7 @@
     python tests/golden/make_golden.py medium     # about an hour on one core
     python tests/golden/make_golden.py batch [K]  # the first K volumes of the uneven batch
     python tests/golden/make_golden.py diff [W]   # the 16 float volumes of 128^3, W threads
+    python tests/golden/make_golden.py convex     # convex pairwise costs, two mid-size volumes
 
 Each file records the workload, the oracle's max-flow value and its surface (in full for
 the small volume; as a SHA-256 of the int32 heights plus their sum otherwise). Nothing
@@ -66,6 +67,21 @@ def record_diff(args):
             "oracle_seconds": round(time.time() - t, 1)}
 
 
+def record_convex(shape):
+    """One volume of the convex workload (edge interval of 10, f(t) = 4 t^2)."""
+    X, Y, Z = shape
+    cost = synth.convex_cost(X, Y, Z)
+    f = synth.convex_profile()
+    t = time.time()
+    r = oracle.solve_convex(cost, synth.CONVEX_DELTA, f)
+    e, ok = oracle.energy_convex(cost, r.heights, synth.CONVEX_DELTA, f)
+    assert ok
+    h = np.ascontiguousarray(r.heights, dtype=np.int32)
+    return {"shape": [X, Y, Z], "delta": synth.CONVEX_DELTA, "f": [int(v) for v in f], "flow": r.flow,
+            "energy": e, "heights_sha256": hashlib.sha256(h.tobytes()).hexdigest(), "heights_sum": int(h.sum()),
+            "oracle_seconds": round(time.time() - t, 1)}
+
+
 def main():
     which = sys.argv[1] if len(sys.argv) > 1 else "small"
     if which == "small":
@@ -92,6 +108,12 @@ def main():
                             "hinge target flat at height 64, margin 1024",
                 "oracle": "explicit-edge Dinic (oracle/pog_oracle.c)",
                 "generator": f"paper_2601_17026_gb300.synth, seed {synth.BASE_SEED}", "volumes": vols}
+    elif which == "convex":
+        data = {"workload": "layered-horizon volumes (synth.convex_cost), convex pairwise cost f(t) = 4 t^2, "
+                            "delta 9 (edge interval of 10)",
+                "oracle": "explicit-edge Dinic on the layered graph (oracle/pog_oracle.c)",
+                "generator": f"paper_2601_17026_gb300.synth, seed {synth.BASE_SEED}",
+                "volumes": [record_convex(s) for s in [(64, 64, 128), (80, 48, 96)]]}
     else:
         raise SystemExit(f"unknown set {which}")
     path = os.path.join(HERE, f"{which}.json")
