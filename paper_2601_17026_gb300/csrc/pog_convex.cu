@@ -31,6 +31,7 @@
 
 #include "pog.h"
 #include "pog_internal.cuh"
+#include "pog_launch.h"
 
 namespace cg = cooperative_groups;
 
@@ -42,9 +43,6 @@ constexpr int kCvLevelBatch = 16;     // BFS levels launched between two host re
 constexpr int kCvOps = 4;             // push/relabel operations per active node and sweep
 constexpr int kCvSweeps = 32;         // default sweeps per global relabel
 constexpr int kCvMaxRounds = 1 << 12;
-constexpr int kCvMark = -2;           // cut extraction: node reached
-
-enum : int { CV_SINK = 0, CV_DOWN, CV_UP, CV_HOUT, CV_HIN, CV_S0, CV_SOUT, CV_SIN };
 
 struct CvCounters {
     unsigned long long src_total;   // sum over z >= 1 of max(-w, 0)
@@ -84,67 +82,155 @@ __device__ __forceinline__ int cv_nb(const CGrid &g, int x, int y, int k, bool &
     }
 }
 
-__device__ __forceinline__ int cv_slot(int kind, int k, int j) { return kind | (k << 4) | (j << 8); }
 
-// Every out-arc of u: f(slot, head (-1 for t), residual). LOAD_INF: the residual of an
-// infinite arc is POG_CAP_INF minus its flow (pushes need the amount); otherwise 1 (the
-// searches only ask whether an arc is residual, and no infinite arc's flow reaches
-// POG_CAP_INF without the solve failing with POG_E_OVERFLOW).
-template <bool LOAD_INF, class F>
-__device__ __forceinline__ void cv_out_arcs(const CGrid &g, int u, int x, int y, int z, F &&f) {
-    f(CV_SINK, -1, __ldcg(g.snk + u));
-    if (z >= 2) f(CV_DOWN, u - 1, LOAD_INF ? POG_CAP_INF - __ldcg(g.fdn + u) : 1);
-    if (z + 1 < g.Z) f(CV_UP, u + 1, __ldcg(g.fdn + u + 1));
-    for (int k = 0; k < 4; ++k) {
-        bool ok;
-        const int off = cv_nb(g, x, y, k, ok);
-        if (!ok) continue;
-        if (z - g.delta >= 1)
-            f(cv_slot(CV_HOUT, k, 0), u + off - g.delta, LOAD_INF ? POG_CAP_INF - __ldcg(g.fh[k] + u) : 1);
-        if (z + g.delta < g.Z) {
-            const int v = u + off + g.delta;
-            f(cv_slot(CV_HIN, k, 0), v, __ldcg(g.fh[k ^ 1] + v));
-        }
-        if (g.k0 > 0) {
-            const int v = u + off;
-            f(cv_slot(CV_S0, k, 0), v,
-              (k & 1) ? g.k0 - __ldcg(g.gs[k >> 1] + u) : g.k0 + __ldcg(g.gs[k >> 1] + v));
-        }
-        for (int j = 0; j < g.nl; ++j) {
-            const int d = g.ld[j];
-            if (z - d >= 1) f(cv_slot(CV_SOUT, k, j), u + off - d, g.lk[j] - __ldcg(flp(g, j, k) + u));
-            if (z + d < g.Z) {
-                const int v = u + off + d;
-                f(cv_slot(CV_SIN, k, j), v, __ldcg(flp(g, j, k ^ 1) + v));
-            }
-        }
+
+// Arc slots. Out-arcs of u: slot 0 sink, 1 down, 2 up, then for direction k the P = 3 + 2 nl
+// slots 3 + k P + r: r = 0 hout, 1 hin, 2 s0, 3 + 2j sout_j, 4 + 2j sin_j (S_out = 3 + 4 P).
+// In-arcs v -> u: slot 0 from (p, z+1), 1 from (p, z-1), then 2 + k P + r: r = 0 the hout of
+// (q, z+D), 1 the reverse of u's hout, 2 s0 from (q, z), 3 + 2j the sout_j of (q, z+d_j),
+// 4 + 2j the reverse of u's sout_j (S_in = 2 + 4 P). A slot decodes to its far end v (-1:
+// the sink) and its residual a + sgn * (*p), or a alone when p is null (infinite arcs in a
+// search, which only asks whether an arc is residual: no infinite arc's flow reaches
+// POG_CAP_INF without the solve failing with POG_E_OVERFLOW). False: no such arc.
+__device__ __forceinline__ int cv_slots_per_dir(const CGrid &g) { return 3 + 2 * g.nl; }
+
+template <bool LOAD_INF>
+__device__ __forceinline__ bool cv_out_slot(const CGrid &g, int u, int x, int y, int z, int s, int P, int &v,
+                                            const int32_t *&p, int &a, int &sgn) {
+    p = nullptr;
+    a = 1;
+    sgn = 1;
+    v = -1;
+    if (s == 0) {
+        p = g.snk + u;
+        a = 0;
+        return true;
     }
+    if (s == 1) {
+        if (z < 2) return false;
+        v = u - 1;
+        if (LOAD_INF) {
+            p = g.fdn + u;
+            a = POG_CAP_INF;
+            sgn = -1;
+        }
+        return true;
+    }
+    if (s == 2) {
+        if (z + 1 >= g.Z) return false;
+        v = u + 1;
+        p = g.fdn + u + 1;
+        a = 0;
+        return true;
+    }
+    const int k = (s - 3) / P, r = (s - 3) - k * P;
+    bool ok;
+    const int off = cv_nb(g, x, y, k, ok);
+    if (!ok) return false;
+    if (r == 0) {
+        if (z - g.delta < 1) return false;
+        v = u + off - g.delta;
+        if (LOAD_INF) {
+            p = g.fh[k] + u;
+            a = POG_CAP_INF;
+            sgn = -1;
+        }
+        return true;
+    }
+    if (r == 1) {
+        if (z + g.delta >= g.Z) return false;
+        v = u + off + g.delta;
+        p = g.fh[k ^ 1] + v;
+        a = 0;
+        return true;
+    }
+    if (r == 2) {
+        if (g.k0 == 0) return false;
+        v = u + off;
+        a = g.k0;
+        if (k & 1) {
+            p = g.gs[k >> 1] + u;
+            sgn = -1;
+        } else {
+            p = g.gs[k >> 1] + v;
+        }
+        return true;
+    }
+    const int j = (r - 3) >> 1, d = g.ld[j];
+    if (((r - 3) & 1) == 0) {
+        if (z - d < 1) return false;
+        v = u + off - d;
+        p = flp(g, j, k) + u;
+        a = g.lk[j];
+        sgn = -1;
+        return true;
+    }
+    if (z + d >= g.Z) return false;
+    v = u + off + d;
+    p = flp(g, j, k ^ 1) + v;
+    a = 0;
+    return true;
 }
 
-// Every in-arc v -> u of u: f(tail, residual of v -> u); infinite arcs report 1.
-template <class F>
-__device__ __forceinline__ void cv_in_arcs(const CGrid &g, int u, int x, int y, int z, F &&f) {
-    if (z + 1 < g.Z) f(u + 1, 1);                        // down arc of (p, z+1)
-    if (z >= 2) f(u - 1, __ldcg(g.fdn + u));             // reverse of u's down arc
-    for (int k = 0; k < 4; ++k) {
-        bool ok;
-        const int off = cv_nb(g, x, y, k, ok);
-        if (!ok) continue;
-        if (z + g.delta < g.Z) f(u + off + g.delta, 1);  // hout_{k^1} of (q, z+D) lands on u
-        if (z - g.delta >= 1) f(u + off - g.delta, __ldcg(g.fh[k] + u));  // reverse of u's hout_k
-        if (g.k0 > 0) {
-            const int v = u + off;
-            f(v, (k & 1) ? g.k0 + __ldcg(g.gs[k >> 1] + u) : g.k0 - __ldcg(g.gs[k >> 1] + v));
-        }
-        for (int j = 0; j < g.nl; ++j) {
-            const int d = g.ld[j];
-            if (z + d < g.Z) {                           // sout_{k^1,j} of (q, z+d) lands on u
-                const int v = u + off + d;
-                f(v, g.lk[j] - __ldcg(flp(g, j, k ^ 1) + v));
-            }
-            if (z - d >= 1) f(u + off - d, __ldcg(flp(g, j, k) + u));  // reverse of u's sout_kj
-        }
+__device__ __forceinline__ bool cv_in_slot(const CGrid &g, int u, int x, int y, int z, int s, int P, int &v,
+                                           const int32_t *&p, int &a, int &sgn) {
+    p = nullptr;
+    a = 1;
+    sgn = 1;
+    if (s == 0) {  // down arc of (p, z+1): infinite
+        if (z + 1 >= g.Z) return false;
+        v = u + 1;
+        return true;
     }
+    if (s == 1) {  // up arc of (p, z-1), the reverse of u's down arc
+        if (z < 2) return false;
+        v = u - 1;
+        p = g.fdn + u;
+        a = 0;
+        return true;
+    }
+    const int k = (s - 2) / P, r = (s - 2) - k * P;
+    bool ok;
+    const int off = cv_nb(g, x, y, k, ok);
+    if (!ok) return false;
+    if (r == 0) {  // hout_{k^1} of (q, z+D) lands on u: infinite
+        if (z + g.delta >= g.Z) return false;
+        v = u + off + g.delta;
+        return true;
+    }
+    if (r == 1) {  // reverse of u's hout_k, from (q, z-D)
+        if (z - g.delta < 1) return false;
+        v = u + off - g.delta;
+        p = g.fh[k] + u;
+        a = 0;
+        return true;
+    }
+    if (r == 2) {  // s0 of q towards p
+        if (g.k0 == 0) return false;
+        v = u + off;
+        a = g.k0;
+        if (k & 1) {
+            p = g.gs[k >> 1] + u;
+        } else {
+            p = g.gs[k >> 1] + v;
+            sgn = -1;
+        }
+        return true;
+    }
+    const int j = (r - 3) >> 1, d = g.ld[j];
+    if (((r - 3) & 1) == 0) {  // sout_{k^1,j} of (q, z+d) lands on u
+        if (z + d >= g.Z) return false;
+        v = u + off + d;
+        p = flp(g, j, k ^ 1) + v;
+        a = g.lk[j];
+        sgn = -1;
+        return true;
+    }
+    if (z - d < 1) return false;  // reverse of u's sout_kj, from (q, z-d)
+    v = u + off - d;
+    p = flp(g, j, k) + u;
+    a = 0;
+    return true;
 }
 
 // Add a to the flow of an infinite arc; true when it reaches POG_CAP_INF.
@@ -153,22 +239,29 @@ __device__ __forceinline__ bool cv_add_inf(int32_t *p, int a) {
     return (long long)old + a >= (long long)POG_CAP_INF;
 }
 
-// Push a units from u along out-arc `slot` with head v (-1: the sink).
-__device__ __forceinline__ void cv_push(const CGrid &g, int u, int slot, int v, int a) {
-    const int kind = slot & 15, k = (slot >> 4) & 15, j = slot >> 8;
+// Push a units from u along out-slot s with far end v (-1: the sink).
+__device__ __forceinline__ void cv_push(const CGrid &g, int u, int s, int P, int v, int a) {
     bool over = false;
-    switch (kind) {
-        case CV_SINK: atomicSub(g.snk + u, a); break;
-        case CV_DOWN: over = cv_add_inf(g.fdn + u, a); break;
-        case CV_UP: atomicSub(g.fdn + u + 1, a); break;
-        case CV_HOUT: over = cv_add_inf(g.fh[k] + u, a); break;
-        case CV_HIN: atomicSub(g.fh[k ^ 1] + v, a); break;
-        case CV_S0:
+    if (s == 0) {
+        atomicSub(g.snk + u, a);
+    } else if (s == 1) {
+        over = cv_add_inf(g.fdn + u, a);
+    } else if (s == 2) {
+        atomicSub(g.fdn + u + 1, a);
+    } else {
+        const int k = (s - 3) / P, r = (s - 3) - k * P;
+        if (r == 0) {
+            over = cv_add_inf(g.fh[k] + u, a);
+        } else if (r == 1) {
+            atomicSub(g.fh[k ^ 1] + v, a);
+        } else if (r == 2) {
             if (k & 1) atomicAdd(g.gs[k >> 1] + u, a);
             else atomicSub(g.gs[k >> 1] + v, a);
-            break;
-        case CV_SOUT: atomicAdd(flp(g, j, k) + u, a); break;
-        default: atomicSub(flp(g, j, k ^ 1) + v, a); break;  // CV_SIN
+        } else {
+            const int j = (r - 3) >> 1;
+            if (((r - 3) & 1) == 0) atomicAdd(flp(g, j, k) + u, a);
+            else atomicSub(flp(g, j, k ^ 1) + v, a);
+        }
     }
     atomicSub(g.exc + u, a);
     if (v >= 0) {
@@ -253,96 +346,127 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_collect(CGrid g, int *list, i
     if (a) cv_append(list, count, u);
 }
 
-// Lock-free push/relabel over the listed nodes (each listed once, so one thread owns a
-// node's excess decrease and its label): find the residual out-arc with the lowest head
-// label; a node not above it is relabelled to that label + 1; then push
-// min(excess, residual) along the arc. A node whose residual arcs all lead to label
-// POG_INF cannot reach the sink and takes that label.
+// Lock-free push/relabel over the listed nodes, one warp per node (each node listed once,
+// so one lane at a time owns its excess decrease, its sink arc and its label). The lanes
+// split the node's out-arc slots; a warp minimum picks the residual arc with the lowest
+// far-end label (ties: the lowest slot). A node not above that label is relabelled to it
+// + 1 (Section 2.1's relabel), then min(excess, residual) is pushed along the arc. A node
+// whose residual arcs all lead to label POG_INF cannot reach the sink and takes that
+// label. Stale reads are safe: every value another thread may change concurrently moves
+// in the direction that makes the push smaller than allowed.
 __global__ void __launch_bounds__(kCvThreads) k_cv_push_relabel(CGrid g, const int *list, const int *count, int ops) {
     const int n = __ldcg(count);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->listed, (unsigned long long)n);
-    for (int i = blockIdx.x * kCvThreads + threadIdx.x; i < n; i += gridDim.x * kCvThreads) {
-        const int u = list[i];
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * kCvThreads + threadIdx.x) >> 5;
+    const int nwarps = gridDim.x * (kCvThreads / 32);
+    const int P = cv_slots_per_dir(g), S = 3 + 4 * P;
+    for (int i = warp; i < n; i += nwarps) {
+        const int u = __ldcg(list + i);
         const int z = u % g.Z, col = u / g.Z;
         const int x = col / g.Y, y = col % g.Y;
         for (int op = 0; op < ops; ++op) {
-            const int e = __ldcg(g.exc + u);
-            int l = __ldcg(g.lab + u);
+            int e = 0, l = 0;
+            if (lane == 0) {
+                e = __ldcg(g.exc + u);
+                l = __ldcg(g.lab + u);
+            }
+            e = __shfl_sync(0xffffffffu, e, 0);
+            l = __shfl_sync(0xffffffffu, l, 0);
             if (e <= 0 || l >= POG_INF) break;
-            int best = POG_INF, bslot = 0, bv = -1, br = 0;
-            cv_out_arcs<true>(g, u, x, y, z, [&](int slot, int v, int r) {
-                if (r <= 0) return;
+            int best = POG_INF, bs = -1, bv = -1, br = 0;
+            for (int s = lane; s < S; s += 32) {
+                int v, a, sgn;
+                const int32_t *p;
+                if (!cv_out_slot<true>(g, u, x, y, z, s, P, v, p, a, sgn)) continue;
+                const int r = p ? a + sgn * __ldcg(p) : a;
+                if (r <= 0) continue;
                 const int lv = v < 0 ? 0 : __ldcg(g.lab + v);
                 if (lv < best) {
                     best = lv;
-                    bslot = slot;
+                    bs = s;
                     bv = v;
                     br = r;
                 }
-            });
-            if (best >= POG_INF) {
-                g.lab[u] = POG_INF;
+            }
+            unsigned long long key = ((unsigned long long)(unsigned)best << 32) | (unsigned)bs;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+                key = other < key ? other : key;
+            }
+            const int wbest = (int)(key >> 32);
+            const int wslot = (int)(unsigned)(key & 0xffffffffu);
+            if (wbest >= POG_INF) {
+                if (lane == 0) g.lab[u] = POG_INF;
                 break;
             }
-            if (l <= best) {
-                l = best + 1;
-                g.lab[u] = l;
+            if (bs == wslot) {  // the one lane that found the arc
+                if (l <= wbest) g.lab[u] = wbest + 1;
+                cv_push(g, u, wslot, P, bv, e < br ? e : br);
             }
-            cv_push(g, u, bslot, bv, e < br ? e : br);
+            __syncwarp();
         }
     }
 }
 
-// Level 0 of the reverse BFS: nodes with a residual sink arc get label 1.
-__global__ void __launch_bounds__(kCvThreads) k_cv_relabel_init(CGrid g, int *q0, int *sizes) {
+// Level 0 of the reverse BFS: nodes with a residual sink arc get label 1 and their visited
+// bit; every other node gets label POG_INF and a clear bit. One warp writes one bitmap word
+// (32 consecutive nodes).
+__global__ void __launch_bounds__(kCvThreads) k_cv_relabel_init(CGrid g, unsigned *visit, int *q0, int *sizes) {
     const int u = blockIdx.x * kCvThreads + threadIdx.x;
     bool a = false;
     if (u < g.N) {
         a = u % g.Z != 0 && __ldcg(g.snk + u) > 0;
         g.lab[u] = a ? 1 : POG_INF;
     }
+    const unsigned bits = __ballot_sync(0xffffffffu, a);
+    if ((threadIdx.x & 31) == 0 && u < g.N) visit[u >> 5] = bits;
     if (a) cv_append(q0, sizes, u);
 }
 
-// Cut extraction, level 0: the nodes that keep excess (z >= 1) are reached; every other
-// node is unmarked (label word 0).
-__global__ void __launch_bounds__(kCvThreads) k_cv_cut_init(CGrid g, int *q0, int *sizes) {
+// Cut extraction, level 0: the nodes that keep excess (z >= 1) are reached.
+__global__ void __launch_bounds__(kCvThreads) k_cv_cut_init(CGrid g, unsigned *visit, int *q0, int *sizes) {
     const int u = blockIdx.x * kCvThreads + threadIdx.x;
-    bool a = false;
-    if (u < g.N) {
-        a = u % g.Z != 0 && __ldcg(g.exc + u) > 0;
-        g.lab[u] = a ? kCvMark : 0;
-    }
+    const bool a = u < g.N && u % g.Z != 0 && __ldcg(g.exc + u) > 0;
+    const unsigned bits = __ballot_sync(0xffffffffu, a);
+    if ((threadIdx.x & 31) == 0 && u < g.N) visit[u >> 5] = bits;
     if (a) cv_append(q0, sizes, u);
 }
 
-// One BFS level over the frontier sizes[level % 3] in qin: REACH = false expands in-arcs
-// (reverse BFS from the sink: an unlabelled tail of a residual arc into the frontier gets
-// label level + 2); REACH = true expands out-arcs (reach of the excess nodes: an unmarked
-// head of a residual arc is marked). New nodes go to qout / sizes[(level + 1) % 3]; the
-// counter of the level after that is cleared here for it.
+// One BFS level, one thread per (frontier node, arc slot) of the frontier sizes[level % 3]
+// in qin. REACH = false: in-arcs (reverse BFS from the sink; a tail not yet visited whose
+// arc into the frontier is residual gets label level + 2). REACH = true: out-arcs (reach
+// of the excess nodes). The visited bit is tested before the residual word is loaded and
+// claimed by an atomic OR; new nodes go to qout / sizes[(level + 1) % 3]. The counter of
+// the level after that is cleared here for it.
 template <bool REACH>
-__global__ void __launch_bounds__(kCvThreads) k_cv_level(CGrid g, const int *qin, int *qout, int *sizes, int level) {
+__global__ void __launch_bounds__(kCvThreads) k_cv_level(CGrid g, unsigned *visit, const int *qin, int *qout,
+                                                         int *sizes, int level) {
     if (blockIdx.x == 0 && threadIdx.x == 0) sizes[(level + 2) % 3] = 0;
     const int n = __ldcg(sizes + level % 3);
     int *nsize = sizes + (level + 1) % 3;
-    const int free_word = REACH ? 0 : POG_INF;
-    const int mark = REACH ? kCvMark : level + 2;
-    for (int i = blockIdx.x * kCvThreads + threadIdx.x; i < n; i += gridDim.x * kCvThreads) {
-        const int u = qin[i];
+    const int P = cv_slots_per_dir(g);
+    const int S = REACH ? 3 + 4 * P : 2 + 4 * P;
+    const long long total = (long long)n * S;
+    const long long stride = (long long)gridDim.x * kCvThreads;
+    for (long long i = (long long)blockIdx.x * kCvThreads + threadIdx.x; i < total; i += stride) {
+        const int u = __ldcg(qin + i / S);
+        const int s = (int)(i % S);
         const int z = u % g.Z, col = u / g.Z;
         const int x = col / g.Y, y = col % g.Y;
-        auto claim = [&](int v, int r) {
-            if (r <= 0 || __ldcg(g.lab + v) != free_word) return;
-            if (atomicCAS(g.lab + v, free_word, mark) == free_word) cv_append(qout, nsize, v);
-        };
-        if (REACH) {
-            cv_out_arcs<false>(g, u, x, y, z, [&](int, int v, int r) {
-                if (v >= 0) claim(v, r);
-            });
-        } else {
-            cv_in_arcs(g, u, x, y, z, claim);
-        }
+        int v, a, sgn;
+        const int32_t *p;
+        const bool ok = REACH ? (s != 0 && cv_out_slot<false>(g, u, x, y, z, s, P, v, p, a, sgn))
+                              : cv_in_slot(g, u, x, y, z, s, P, v, p, a, sgn);
+        if (!ok) continue;
+        const unsigned bit = 1u << (v & 31);
+        if (__ldcg(visit + (v >> 5)) & bit) continue;
+        const int r = p ? a + sgn * __ldcg(p) : a;
+        if (r <= 0) continue;
+        if (atomicOr(visit + (v >> 5), bit) & bit) continue;
+        if (!REACH) g.lab[v] = level + 2;
+        cv_append(qout, nsize, v);
     }
 }
 
@@ -358,13 +482,18 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_excess_sum(CGrid g) {
 }
 
 // Surface: the top reached node of each column (0 when only the bottom layer is).
-__global__ void __launch_bounds__(kCvThreads) k_cv_heights(CGrid g, int32_t *heights) {
+__global__ void __launch_bounds__(kCvThreads) k_cv_heights(CGrid g, const unsigned *visit, int32_t *heights) {
     const int col = blockIdx.x * kCvThreads + threadIdx.x;
     if (col >= g.X * g.Y) return;
     int h = 0;
-    const int32_t *lab = g.lab + (size_t)col * g.Z;
-    for (int z = 1; z < g.Z; ++z)
-        if (lab[z] == kCvMark) h = z;
+    const long long base = (long long)col * g.Z;
+    for (int z = g.Z - 1; z >= 1; --z) {
+        const long long v = base + z;
+        if ((__ldcg(visit + (v >> 5)) >> (v & 31)) & 1u) {
+            h = z;
+            break;
+        }
+    }
     heights[col] = h;
 }
 
@@ -398,11 +527,14 @@ struct CvSolve {
     cudaStream_t st = nullptr;
     void *arena = nullptr;
     int *qa = nullptr, *qb = nullptr, *list = nullptr, *count = nullptr, *sizes = nullptr;
+    unsigned *visit = nullptr;          // one bit per node: visited by the current search
+    pog::DevCounters *pctr = nullptr;   // error word of the column pre-push
     int persist_blocks = 0;         // grid of the grid-stride kernels: 8 blocks per SM
     bool timing = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     pog_stats_t stats{};
     CvCounters host_ctr{};
+    int host_perr = 0;
     int host_int = 0;
 
     ~CvSolve() {
@@ -438,7 +570,9 @@ struct CvSolve {
 
     pog_status read_counters() {
         CV_TRY_CUDA(cudaMemcpyAsync(&host_ctr, g.ctr, sizeof(CvCounters), cudaMemcpyDeviceToHost, st));
+        CV_TRY_CUDA(cudaMemcpyAsync(&host_perr, &pctr->error, sizeof(int), cudaMemcpyDeviceToHost, st));
         CV_TRY_CUDA(cudaStreamSynchronize(st));
+        if (host_perr) return POG_E_OVERFLOW;
         if (host_ctr.error & POG_ERR_COST_RANGE) return POG_E_OVERFLOW;
         if (host_ctr.error & POG_ERR_FLOW_RANGE) return POG_E_OVERFLOW;
         if (host_ctr.error) return POG_E_CUDA;
@@ -454,7 +588,7 @@ struct CvSolve {
             for (int i = 0; i < kCvLevelBatch; ++i, ++level) {
                 const int *qin = (level & 1) ? qb : qa;
                 int *qout = (level & 1) ? qa : qb;
-                k_cv_level<REACH><<<persist_blocks, kCvThreads, 0, st>>>(g, qin, qout, sizes, level);
+                k_cv_level<REACH><<<persist_blocks, kCvThreads, 0, st>>>(g, visit, qin, qout, sizes, level);
                 CV_TRY_CUDA(cudaGetLastError());
                 stats.launches++;
             }
@@ -469,7 +603,7 @@ struct CvSolve {
     pog_status global_relabel() {
         CV_TRY(begin_timer());
         CV_TRY_CUDA(cudaMemsetAsync(sizes, 0, 3 * sizeof(int), st));
-        k_cv_relabel_init<<<cv_blocks(g.N), kCvThreads, 0, st>>>(g, qa, sizes);
+        k_cv_relabel_init<<<cv_blocks(g.N), kCvThreads, 0, st>>>(g, visit, qa, sizes);
         CV_TRY_CUDA(cudaGetLastError());
         stats.launches++;
         CV_TRY(levels<false>(&stats.bfs_passes));
@@ -501,11 +635,11 @@ struct CvSolve {
     pog_status cut(int32_t *heights) {
         CV_TRY(begin_timer());
         CV_TRY_CUDA(cudaMemsetAsync(sizes, 0, 3 * sizeof(int), st));
-        k_cv_cut_init<<<cv_blocks(g.N), kCvThreads, 0, st>>>(g, qa, sizes);
+        k_cv_cut_init<<<cv_blocks(g.N), kCvThreads, 0, st>>>(g, visit, qa, sizes);
         CV_TRY_CUDA(cudaGetLastError());
         stats.launches++;
         CV_TRY(levels<true>(&stats.cut_passes));
-        k_cv_heights<<<cv_blocks((long long)g.X * g.Y), kCvThreads, 0, st>>>(g, heights);
+        k_cv_heights<<<cv_blocks((long long)g.X * g.Y), kCvThreads, 0, st>>>(g, visit, heights);
         CV_TRY_CUDA(cudaGetLastError());
         k_cv_excess_sum<<<cv_blocks(g.N), kCvThreads, 0, st>>>(g);
         CV_TRY_CUDA(cudaGetLastError());
@@ -567,8 +701,9 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     // flow words, zeroed in one memset) | qa qb list.
     const size_t arr = cv_align((size_t)N * 4);
     const int flow_arrays = 1 + 4 + 2 + 4 * g.nl;
-    const size_t head = cv_align(sizeof(CvCounters)) + cv_align(4 * sizeof(int));
-    const size_t bytes = head + (3 + flow_arrays + 3) * arr;
+    const size_t head = cv_align(sizeof(CvCounters)) + cv_align(4 * sizeof(int)) + cv_align(sizeof(pog::DevCounters));
+    const size_t bits = cv_align(((size_t)N + 31) / 32 * 4);
+    const size_t bytes = head + (3 + flow_arrays + 3) * arr + bits;
     if (opt && opt->test_fail_alloc == 1) return POG_E_NOMEM;
     if (cudaMalloc(&s.arena, bytes) != cudaSuccess) {
         s.arena = nullptr;
@@ -579,6 +714,7 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     g.ctr = reinterpret_cast<CvCounters *>(p);
     s.count = reinterpret_cast<int *>(p + cv_align(sizeof(CvCounters)));
     s.sizes = s.count + 1;
+    s.pctr = reinterpret_cast<pog::DevCounters *>(p + cv_align(sizeof(CvCounters)) + cv_align(4 * sizeof(int)));
     p += head;
     auto take = [&]() {
         int32_t *r = reinterpret_cast<int32_t *>(p);
@@ -599,6 +735,8 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     s.qa = take();
     s.qb = take();
     s.list = take();
+    s.visit = reinterpret_cast<unsigned *>(p);
+    p += bits;
     s.stats.nodes = N;
     s.stats.state_bytes = (long long)bytes;
 
@@ -608,6 +746,21 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     k_cv_build<<<cv_blocks(N), kCvThreads, 0, s.st>>>(g, cost_dev);
     CV_TRY_CUDA(cudaGetLastError());
     s.stats.launches++;
+    if (!(opt && (opt->flags & POG_FLAG_NO_PREPUSH))) {
+        // Column pre-push along the infinite down arcs (the kernel of pog_build's solve, on a
+        // view of this state: it touches only exc, snk and fdn, and the error word).
+        pog::Grid view{};
+        view.X = X;
+        view.Y = Y;
+        view.Z = Z;
+        view.N = g.N;
+        view.exc = g.exc;
+        view.snk = g.snk;
+        view.fdn = g.fdn;
+        view.ctr = s.pctr;
+        CV_TRY_CUDA(pog::launch_column_prepush(view, s.st));
+        s.stats.launches++;
+    }
     CV_TRY(s.end_timer(&s.stats.build_ms));
     CV_TRY(s.read_counters());
     int32_t c000 = 0;
