@@ -39,9 +39,12 @@ namespace {
 
 constexpr int kCvThreads = 256;
 constexpr int kCvMaxLayers = POG_CONVEX_MAX_DELTA;
-constexpr int kCvLevelBatch = 16;     // BFS levels launched between two host reads of the frontier size
+constexpr int kCvLevelBatch = 32;     // BFS levels launched between two host reads of the frontier size
 constexpr int kCvOps = 4;             // push/relabel operations per active node and sweep
-constexpr int kCvSweeps = 32;         // default sweeps per global relabel
+// Out-arc slots per lane in the push step: 32 * kCvPasses >= 3 + 4 * (3 + 2 * 31), the
+// slots of a node with every layer d = 1..31 present.
+constexpr int kCvPasses = 9;
+constexpr int kCvSweeps = 64;         // default sweeps per global relabel
 constexpr int kCvMaxRounds = 1 << 12;
 
 struct CvCounters {
@@ -374,21 +377,34 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_push_relabel(CGrid g, const i
             e = __shfl_sync(0xffffffffu, e, 0);
             l = __shfl_sync(0xffffffffu, l, 0);
             if (e <= 0 || l >= POG_INF) break;
-            int best = POG_INF, bs = -1, bv = -1, br = 0;
-            for (int s = lane; s < S; s += 32) {
+            // All residual words of this lane's slots first, then the far-end labels of the
+            // residual ones: two rounds of independent loads instead of a chain per slot.
+            int vv[kCvPasses], rr[kCvPasses];
+#pragma unroll
+            for (int t = 0; t < kCvPasses; ++t) {
+                const int s = lane + 32 * t;
+                vv[t] = -2;
+                rr[t] = 0;
                 int v, a, sgn;
                 const int32_t *p;
-                if (!cv_out_slot<true>(g, u, x, y, z, s, P, v, p, a, sgn)) continue;
-                const int r = p ? a + sgn * __ldcg(p) : a;
-                if (r <= 0) continue;
-                const int lv = v < 0 ? 0 : __ldcg(g.lab + v);
-                if (lv < best) {
-                    best = lv;
-                    bs = s;
-                    bv = v;
-                    br = r;
+                if (s < S && cv_out_slot<true>(g, u, x, y, z, s, P, v, p, a, sgn)) {
+                    vv[t] = v;
+                    rr[t] = p ? a + sgn * __ldcg(p) : a;
                 }
             }
+            int ll[kCvPasses];
+#pragma unroll
+            for (int t = 0; t < kCvPasses; ++t)
+                ll[t] = rr[t] <= 0 ? POG_INF : (vv[t] < 0 ? 0 : __ldcg(g.lab + vv[t]));
+            int best = POG_INF, bs = -1, bv = -1, br = 0;
+#pragma unroll
+            for (int t = 0; t < kCvPasses; ++t)
+                if (ll[t] < best) {
+                    best = ll[t];
+                    bs = lane + 32 * t;
+                    bv = vv[t];
+                    br = rr[t];
+                }
             unsigned long long key = ((unsigned long long)(unsigned)best << 32) | (unsigned)bs;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -775,7 +791,11 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
         if (round == 0) s.stats.active_initial = active;
         CV_TRY(s.read_counters());
         if (active == 0) break;
-        if (round + 1 >= max_rounds) return POG_E_NOCONVERGE;
+        if (round + 1 >= max_rounds) {
+            s.stats.tiles_visited = (long long)s.host_ctr.listed;
+            if (stats_out) *stats_out = s.stats;
+            return POG_E_NOCONVERGE;
+        }
         CV_TRY(s.sweeps(sweeps_per_round));
     }
     CV_TRY(s.cut(heights_dev));
