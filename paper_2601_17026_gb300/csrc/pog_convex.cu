@@ -41,9 +41,9 @@ constexpr int kCvThreads = 256;
 constexpr int kCvMaxLayers = POG_CONVEX_MAX_DELTA;
 constexpr int kCvLevelBatch = 32;     // BFS levels launched between two host reads of the frontier size
 constexpr int kCvOps = 4;             // push/relabel operations per active node and sweep
-// Out-arc slots per lane in the push step: 32 * kCvPasses >= 3 + 4 * (3 + 2 * 31), the
-// slots of a node with every layer d = 1..31 present.
-constexpr int kCvPasses = 9;
+// Out-arc slots per lane in the push step, at most: 32 * kCvMaxPasses >= 3 + 4 * (3 + 2 * 31),
+// the slots of a node with every layer d = 1..31 present.
+constexpr int kCvMaxPasses = 9;
 constexpr int kCvSweeps = 64;         // default sweeps per global relabel
 constexpr int kCvMaxRounds = 1 << 12;
 
@@ -97,19 +97,16 @@ __device__ __forceinline__ int cv_nb(const CGrid &g, int x, int y, int k, bool &
 // POG_CAP_INF without the solve failing with POG_E_OVERFLOW). False: no such arc.
 __device__ __forceinline__ int cv_slots_per_dir(const CGrid &g) { return 3 + 2 * g.nl; }
 
+// Column out-arcs of u: r = 0 sink, 1 down, 2 up.
 template <bool LOAD_INF>
-__device__ __forceinline__ bool cv_out_slot(const CGrid &g, int u, int x, int y, int z, int s, int P, int &v,
-                                            const int32_t *&p, int &a, int &sgn) {
-    p = nullptr;
-    a = 1;
-    sgn = 1;
-    v = -1;
-    if (s == 0) {
+__device__ __forceinline__ bool cv_out_column(const CGrid &g, int u, int z, int r, int &v, const int32_t *&p, int &a,
+                                              int &sgn) {
+    if (r == 0) {
         p = g.snk + u;
         a = 0;
         return true;
     }
-    if (s == 1) {
+    if (r == 1) {
         if (z < 2) return false;
         v = u - 1;
         if (LOAD_INF) {
@@ -119,14 +116,23 @@ __device__ __forceinline__ bool cv_out_slot(const CGrid &g, int u, int x, int y,
         }
         return true;
     }
-    if (s == 2) {
-        if (z + 1 >= g.Z) return false;
-        v = u + 1;
-        p = g.fdn + u + 1;
-        a = 0;
-        return true;
-    }
-    const int k = (s - 3) / P, r = (s - 3) - k * P;
+    if (z + 1 >= g.Z) return false;
+    v = u + 1;
+    p = g.fdn + u + 1;
+    a = 0;
+    return true;
+}
+
+// Out-arc of u by direction k and position r within it (k = -1: the column slots, r = 0
+// sink, 1 down, 2 up).
+template <bool LOAD_INF>
+__device__ __forceinline__ bool cv_out_arc(const CGrid &g, int u, int x, int y, int z, int k, int r, int &v,
+                                           const int32_t *&p, int &a, int &sgn) {
+    p = nullptr;
+    a = 1;
+    sgn = 1;
+    v = -1;
+    if (k < 0) return cv_out_column<LOAD_INF>(g, u, z, r, v, p, a, sgn);
     bool ok;
     const int off = cv_nb(g, x, y, k, ok);
     if (!ok) return false;
@@ -174,6 +180,15 @@ __device__ __forceinline__ bool cv_out_slot(const CGrid &g, int u, int x, int y,
     a = 0;
     return true;
 }
+
+template <bool LOAD_INF>
+__device__ __forceinline__ bool cv_out_slot(const CGrid &g, int u, int x, int y, int z, int s, int P, int &v,
+                                            const int32_t *&p, int &a, int &sgn) {
+    if (s < 3) return cv_out_arc<LOAD_INF>(g, u, x, y, z, -1, s, v, p, a, sgn);
+    const int k = (s - 3) / P;
+    return cv_out_arc<LOAD_INF>(g, u, x, y, z, k, (s - 3) - k * P, v, p, a, sgn);
+}
+
 
 __device__ __forceinline__ bool cv_in_slot(const CGrid &g, int u, int x, int y, int z, int s, int P, int &v,
                                            const int32_t *&p, int &a, int &sgn) {
@@ -357,13 +372,23 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_collect(CGrid g, int *list, i
 // whose residual arcs all lead to label POG_INF cannot reach the sink and takes that
 // label. Stale reads are safe: every value another thread may change concurrently moves
 // in the direction that makes the push smaller than allowed.
-__global__ void __launch_bounds__(kCvThreads) k_cv_push_relabel(CGrid g, const int *list, const int *count, int ops) {
+// PASSES = ceil(S_out / 32) slots per lane; each lane's slots are decoded into (direction,
+// position) once, before the node loop.
+template <int PASSES>
+__global__ void __launch_bounds__(kCvThreads, 4) k_cv_push_relabel(CGrid g, const int *list, const int *count, int ops) {
     const int n = __ldcg(count);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->listed, (unsigned long long)n);
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * kCvThreads + threadIdx.x) >> 5;
     const int nwarps = gridDim.x * (kCvThreads / 32);
     const int P = cv_slots_per_dir(g), S = 3 + 4 * P;
+    int kk[PASSES], rq[PASSES];  // kk = -2: no slot; -1: column slot rq
+#pragma unroll
+    for (int t = 0; t < PASSES; ++t) {
+        const int s = lane + 32 * t;
+        kk[t] = s >= S ? -2 : (s < 3 ? -1 : (s - 3) / P);
+        rq[t] = s < 3 ? s : (s - 3) - (kk[t] < 0 ? 0 : kk[t]) * P;
+    }
     for (int i = warp; i < n; i += nwarps) {
         const int u = __ldcg(list + i);
         const int z = u % g.Z, col = u / g.Z;
@@ -379,26 +404,25 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_push_relabel(CGrid g, const i
             if (e <= 0 || l >= POG_INF) break;
             // All residual words of this lane's slots first, then the far-end labels of the
             // residual ones: two rounds of independent loads instead of a chain per slot.
-            int vv[kCvPasses], rr[kCvPasses];
+            int vv[PASSES], rr[PASSES];
 #pragma unroll
-            for (int t = 0; t < kCvPasses; ++t) {
-                const int s = lane + 32 * t;
+            for (int t = 0; t < PASSES; ++t) {
                 vv[t] = -2;
                 rr[t] = 0;
                 int v, a, sgn;
                 const int32_t *p;
-                if (s < S && cv_out_slot<true>(g, u, x, y, z, s, P, v, p, a, sgn)) {
+                if (kk[t] != -2 && cv_out_arc<true>(g, u, x, y, z, kk[t], rq[t], v, p, a, sgn)) {
                     vv[t] = v;
                     rr[t] = p ? a + sgn * __ldcg(p) : a;
                 }
             }
-            int ll[kCvPasses];
+            int ll[PASSES];
 #pragma unroll
-            for (int t = 0; t < kCvPasses; ++t)
+            for (int t = 0; t < PASSES; ++t)
                 ll[t] = rr[t] <= 0 ? POG_INF : (vv[t] < 0 ? 0 : __ldcg(g.lab + vv[t]));
             int best = POG_INF, bs = -1, bv = -1, br = 0;
 #pragma unroll
-            for (int t = 0; t < kCvPasses; ++t)
+            for (int t = 0; t < PASSES; ++t)
                 if (ll[t] < best) {
                     best = ll[t];
                     bs = lane + 32 * t;
@@ -636,12 +660,28 @@ struct CvSolve {
         return POG_OK;
     }
 
+    cudaError_t launch_push(const CGrid &gg, const int *l, const int *c) {
+        const int passes = (3 + 4 * (3 + 2 * gg.nl) + 31) / 32;
+        const dim3 grid(persist_blocks), block(kCvThreads);
+        switch (passes) {
+            case 1: k_cv_push_relabel<1><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 2: k_cv_push_relabel<2><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 3: k_cv_push_relabel<3><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 4: k_cv_push_relabel<4><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 5: k_cv_push_relabel<5><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 6: k_cv_push_relabel<6><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 7: k_cv_push_relabel<7><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 8: k_cv_push_relabel<8><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            default: k_cv_push_relabel<kCvMaxPasses><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+        }
+        return cudaGetLastError();
+    }
+
     pog_status sweeps(int n) {
         CV_TRY(begin_timer());
         for (int s = 0; s < n; ++s) {
             if (s > 0) CV_TRY(collect(false, nullptr));
-            k_cv_push_relabel<<<persist_blocks, kCvThreads, 0, st>>>(g, list, count, kCvOps);
-            CV_TRY_CUDA(cudaGetLastError());
+            CV_TRY_CUDA(launch_push(g, list, count));
             stats.launches++;
             stats.sweeps++;
         }
