@@ -163,13 +163,17 @@ MEASURED_TRAFFIC = {
     "k_tile_push_relabel": {"bytes_per_unit": 63479, "unit": "tile visit", "source_sha": "80e2f306e500ec0b"},
     # the global relabel after those 64 sweeps: 4.57 GB over 25,165,824 nodes
     "k_global_relabel": {"bytes_per_unit": 181.4, "unit": "node", "source_sha": "ee6bef5d91380cd9"},
+    # convex solve, 128x128x128 (delta 9, f(t) = 4 t^2): the 64 push launches between the first two
+    # global relabels, 6.92 GB over 5,532,113 listed nodes
+    "k_cv_push_relabel": {"bytes_per_unit": 1250.9, "unit": "listed node", "source_sha": "3e3c2d8a8aeb826c"},
 }
 
 
 def _source_sha(kernel):
     import hashlib
 
-    src = {"k_tile_push_relabel": "pog_tile.cu", "k_global_relabel": "pog_bfs.cu"}.get(kernel)
+    src = {"k_tile_push_relabel": "pog_tile.cu", "k_global_relabel": "pog_bfs.cu",
+           "k_cv_push_relabel": "pog_convex.cu"}.get(kernel)
     if src is None:
         return None
     h = hashlib.sha256()
@@ -509,9 +513,13 @@ def convex_leg(args, warmup=1, steps=3):
     nl = int(np.count_nonzero(np.diff(np.concatenate([[0], f]), 2)))  # layers d >= 1 with k_d > 0
     arcs = 3 + 4 * (2 + int(f[0] > 0) + 2 * nl)  # out-arcs of an interior node
     per_node = 20 + 8 * arcs  # exc, lab, each arc word and head label; three atomic words
-    sweep_bytes = st["tiles_visited"] * per_node + st["sweeps"] * 8 * (n - X * Y)
+    sweeps = max(int(st["sweeps"]), 1)
+    scan = 8 * (n - X * Y)  # k_cv_collect: excess and label of every node above the bottom layer
+    sweep_bytes = st["tiles_visited"] * per_node + sweeps * scan
     peak, peak_src = _peaks()
     achieved = sweep_bytes / (st["sweep_ms"] / 1e3) / 1e9 if st["sweep_ms"] > 0 else 0.0
+    push_traffic = measured_traffic("k_cv_push_relabel", st["tiles_visited"] / sweeps)
+    traffic = None if push_traffic is None else int(push_traffic + scan)
     fv = np.concatenate([[0], f])
     hn = h.cpu().numpy()
     e_def = _energy_pairwise(cost_np, hn, fv)
@@ -522,10 +530,12 @@ def convex_leg(args, warmup=1, steps=3):
            "listed_nodes": st["tiles_visited"],
            "kernel_ms": {"sweep": round(st["sweep_ms"], 1), "relabel": round(st["bfs_ms"], 1),
                          "cut": round(st["cut_ms"], 1), "build": round(st["build_ms"], 1)},
-           "roofline": {"bound": "hbm", "kernel": "k_cv_push_relabel + k_cv_collect",
+           "roofline": {"bound": "hbm", "kernel": "k_cv_collect + k_cv_push_relabel (one sweep)",
                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
-                        "bytes_per_listed_node": per_node},
+                        "frac": round(achieved / peak, 4), "traffic": traffic,
+                        "traffic_ratio": None if traffic is None else round(traffic / (sweep_bytes / sweeps), 2),
+                        "bytes_per_launch": int(sweep_bytes / sweeps), "avg_launch_ms": round(st["sweep_ms"] / sweeps, 4),
+                        "peak_source": peak_src, "bytes_per_listed_node": per_node},
            "energy_identity": "holds" if e_def == energy else f"DIFFERS ({e_def} vs {energy})"}
     gold = os.path.join(ROOT, "tests", "golden", "convex.json")
     if os.path.exists(gold):
