@@ -399,9 +399,7 @@ POG_API pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int32_t
  *   f_host      : host, int64 [delta]: f(1), ..., f(delta) (may be NULL when delta = 0).
  *                 POG_E_INVALID unless 0 <= k_d < 2^30 for every d (f convex, f(1) >= 0).
  *   opt         : host, may be NULL. Used: sweeps_per_relabel (default 64), max_rounds,
- *                 tile_sweeps (here: push/relabel operations per active node and sweep,
- *                 default 4, at most 64), flags (POG_FLAG_TIMING, POG_FLAG_NO_PREPUSH),
- *                 test_fail_alloc (1: the state allocation fails).
+ *                 flags (POG_FLAG_TIMING), test_fail_alloc (1: the state allocation fails).
  *   stream      : cudaStream_t for all device work.
  *   flow_out    : host, receives the max-flow value of the literal s-t graph.
  *   energy_out  : host, may be NULL: receives E*(h) = max-flow - K (K as for pog_energy).
@@ -410,7 +408,7 @@ POG_API pog_status pog_solve_noalloc(const int32_t *cost_dev, int32_t X, int32_t
  *                 tiles, and its tiles_visited field counts the active nodes listed for the
  *                 push/relabel sweeps, summed over the sweeps. Also filled when the call
  *                 returns POG_E_NOCONVERGE (the counters up to the round cap).
- * Allocates (10 + 4 L) * 4 + 20 bytes per node on the device (L = layers d >= 1 with
+ * Allocates (10 + 4 L) * 4 + 12 bytes per node on the device (L = layers d >= 1 with
  * k_d > 0) and frees them before returning; blocks until the work on `stream` is done.
  */
 #define POG_CONVEX_MAX_DELTA 32

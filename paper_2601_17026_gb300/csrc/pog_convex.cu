@@ -257,9 +257,8 @@ __device__ __forceinline__ bool cv_add_inf(int32_t *p, int a) {
     return (long long)old + a >= (long long)POG_CAP_INF;
 }
 
-// Push a units from u along out-slot s with far end v (-1: the sink). Returns v's excess
-// before the push (0 for the sink).
-__device__ __forceinline__ int cv_push(const CGrid &g, int u, int s, int P, int v, int a) {
+// Push a units from u along out-slot s with far end v (-1: the sink).
+__device__ __forceinline__ void cv_push(const CGrid &g, int u, int s, int P, int v, int a) {
     bool over = false;
     if (s == 0) {
         atomicSub(g.snk + u, a);
@@ -283,15 +282,12 @@ __device__ __forceinline__ int cv_push(const CGrid &g, int u, int s, int P, int 
         }
     }
     atomicSub(g.exc + u, a);
-    int old = 0;
     if (v >= 0) {
-        old = atomicAdd(g.exc + v, a);
+        const int old = atomicAdd(g.exc + v, a);
         if ((long long)old + a > 0x7fffffffLL) over = true;
     }
     if (over) atomicOr(&g.ctr->error, POG_ERR_FLOW_RANGE);
-    return old;
 }
-
 
 // One warp-aggregated append of v to a queue.
 __device__ __forceinline__ void cv_append(int *queue, int *size, int v) {
@@ -301,17 +297,6 @@ __device__ __forceinline__ void cv_append(int *queue, int *size, int v) {
     base = grp.shfl(base, 0);
     queue[base + (int)grp.thread_rank()] = v;
 }
-
-// The list of the next sweep: node v enters it once, claimed through its epoch word.
-struct CvNext {
-    int *list;    // null: no list is built (the sweep before a global relabel)
-    int *count;
-    int *epoch;   // per node: the last sweep whose list it entered
-    int serial;   // the next sweep's number
-    __device__ __forceinline__ void claim(int v) const {
-        if (atomicMax(epoch + v, serial) < serial) cv_append(list, count, v);
-    }
-};
 
 __device__ __forceinline__ unsigned long long cv_warp_sum(unsigned long long v) {
 #pragma unroll
@@ -388,14 +373,9 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_collect(CGrid g, int *list, i
 // label. Stale reads are safe: every value another thread may change concurrently moves
 // in the direction that makes the push smaller than allowed.
 // PASSES = ceil(S_out / 32) slots per lane; each lane's slots are decoded into (direction,
-// position) once, before the node loop. The list of the next sweep is built here instead of
-// by a scan: a push into a node without excess lists that node, and a node that keeps
-// excess after its operations lists itself. Every node with excess and a finite label after
-// this sweep is then listed (a push that finds excess already there comes after its owner's
-// final read, which saw it, or before a push that found none).
+// position) once, before the node loop.
 template <int PASSES>
-__global__ void __launch_bounds__(kCvThreads, 4) k_cv_push_relabel(CGrid g, const int *list, const int *count, int ops,
-                                                                   CvNext next) {
+__global__ void __launch_bounds__(kCvThreads, 4) k_cv_push_relabel(CGrid g, const int *list, const int *count, int ops) {
     const int n = __ldcg(count);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->listed, (unsigned long long)n);
     const int lane = threadIdx.x & 31;
@@ -463,13 +443,10 @@ __global__ void __launch_bounds__(kCvThreads, 4) k_cv_push_relabel(CGrid g, cons
             }
             if (bs == wslot) {  // the one lane that found the arc
                 if (l <= wbest) g.lab[u] = wbest + 1;
-                const int old = cv_push(g, u, wslot, P, bv, e < br ? e : br);
-                if (next.list && bv >= 0 && old == 0) next.claim(bv);
+                cv_push(g, u, wslot, P, bv, e < br ? e : br);
             }
             __syncwarp();
         }
-        if (next.list && lane == 0 && __ldcg(g.exc + u) > 0 && __ldcg(g.lab + u) < POG_INF) next.claim(u);
-        __syncwarp();
     }
 }
 
@@ -590,12 +567,9 @@ struct CvSolve {
     cudaStream_t st = nullptr;
     void *arena = nullptr;
     int *qa = nullptr, *qb = nullptr, *list = nullptr, *count = nullptr, *sizes = nullptr;
-    int *list2 = nullptr, *count2 = nullptr, *epoch = nullptr;  // the sweeps' second list; list epochs
-    int serial = 0;                                               // sweeps that built a list
     unsigned *visit = nullptr;          // one bit per node: visited by the current search
     pog::DevCounters *pctr = nullptr;   // error word of the column pre-push
     int persist_blocks = 0;         // grid of the grid-stride kernels: 8 blocks per SM
-    int ops = kCvOps;               // push/relabel operations per listed node and sweep
     bool timing = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     pog_stats_t stats{};
@@ -686,46 +660,30 @@ struct CvSolve {
         return POG_OK;
     }
 
-    cudaError_t launch_push(const CGrid &gg, const int *l, const int *c, const CvNext &nx) {
+    cudaError_t launch_push(const CGrid &gg, const int *l, const int *c) {
         const int passes = (3 + 4 * (3 + 2 * gg.nl) + 31) / 32;
         const dim3 grid(persist_blocks), block(kCvThreads);
         switch (passes) {
-            case 1: k_cv_push_relabel<1><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 2: k_cv_push_relabel<2><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 3: k_cv_push_relabel<3><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 4: k_cv_push_relabel<4><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 5: k_cv_push_relabel<5><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 6: k_cv_push_relabel<6><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 7: k_cv_push_relabel<7><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            case 8: k_cv_push_relabel<8><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
-            default: k_cv_push_relabel<kCvMaxPasses><<<grid, block, 0, st>>>(gg, l, c, ops, nx); break;
+            case 1: k_cv_push_relabel<1><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 2: k_cv_push_relabel<2><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 3: k_cv_push_relabel<3><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 4: k_cv_push_relabel<4><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 5: k_cv_push_relabel<5><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 6: k_cv_push_relabel<6><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 7: k_cv_push_relabel<7><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            case 8: k_cv_push_relabel<8><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
+            default: k_cv_push_relabel<kCvMaxPasses><<<grid, block, 0, st>>>(gg, l, c, kCvOps); break;
         }
         return cudaGetLastError();
     }
 
-    // n sweeps from the list that collect() left in list / count; each sweep lists the nodes
-    // of the next one (into the other list), except the last, which a global relabel follows.
     pog_status sweeps(int n) {
         CV_TRY(begin_timer());
-        int *cl = list, *cc = count, *nl = list2, *nc = count2;
         for (int s = 0; s < n; ++s) {
-            CvNext nx{};
-            if (s + 1 < n) {
-                CV_TRY_CUDA(cudaMemsetAsync(nc, 0, sizeof(int), st));
-                nx.list = nl;
-                nx.count = nc;
-                nx.epoch = epoch;
-                nx.serial = ++serial;
-            }
-            CV_TRY_CUDA(launch_push(g, cl, cc, nx));
+            if (s > 0) CV_TRY(collect(false, nullptr));
+            CV_TRY_CUDA(launch_push(g, list, count));
             stats.launches++;
             stats.sweeps++;
-            int *t = cl;
-            cl = nl;
-            nl = t;
-            t = cc;
-            cc = nc;
-            nc = t;
         }
         return end_timer(&stats.sweep_ms);
     }
@@ -784,7 +742,6 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     const int sweeps_per_round = opt && opt->sweeps_per_relabel > 0 ? opt->sweeps_per_relabel : kCvSweeps;
     const int max_rounds = opt && opt->max_rounds > 0 ? opt->max_rounds : kCvMaxRounds;
     s.timing = opt && (opt->flags & POG_FLAG_TIMING);
-    if (opt && opt->tile_sweeps > 0) s.ops = opt->tile_sweeps < 64 ? opt->tile_sweeps : 64;
     s.st = static_cast<cudaStream_t>(stream);
 
     int dev = 0, sms = 0;
@@ -802,7 +759,7 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     const int flow_arrays = 1 + 4 + 2 + 4 * g.nl;
     const size_t head = cv_align(sizeof(CvCounters)) + cv_align(4 * sizeof(int)) + cv_align(sizeof(pog::DevCounters));
     const size_t bits = cv_align(((size_t)N + 31) / 32 * 4);
-    const size_t bytes = head + (3 + flow_arrays + 5) * arr + bits;
+    const size_t bytes = head + (3 + flow_arrays + 3) * arr + bits;
     if (opt && opt->test_fail_alloc == 1) return POG_E_NOMEM;
     if (cudaMalloc(&s.arena, bytes) != cudaSuccess) {
         s.arena = nullptr;
@@ -813,7 +770,6 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     g.ctr = reinterpret_cast<CvCounters *>(p);
     s.count = reinterpret_cast<int *>(p + cv_align(sizeof(CvCounters)));
     s.sizes = s.count + 1;
-    s.count2 = s.count + 4;
     s.pctr = reinterpret_cast<pog::DevCounters *>(p + cv_align(sizeof(CvCounters)) + cv_align(4 * sizeof(int)));
     p += head;
     auto take = [&]() {
@@ -835,8 +791,6 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
     s.qa = take();
     s.qb = take();
     s.list = take();
-    s.list2 = take();
-    s.epoch = take();
     s.visit = reinterpret_cast<unsigned *>(p);
     p += bits;
     s.stats.nodes = N;
@@ -844,7 +798,6 @@ extern "C" POG_API pog_status pog_solve_convex(const int32_t *cost_dev, int32_t 
 
     CV_TRY_CUDA(cudaMemsetAsync(s.arena, 0, head, s.st));
     CV_TRY_CUDA(cudaMemsetAsync(flow_begin, 0, flow_bytes, s.st));
-    CV_TRY_CUDA(cudaMemsetAsync(s.epoch, 0, (size_t)N * 4, s.st));
     CV_TRY(s.begin_timer());
     k_cv_build<<<cv_blocks(N), kCvThreads, 0, s.st>>>(g, cost_dev);
     CV_TRY_CUDA(cudaGetLastError());
