@@ -327,15 +327,24 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, vol)
     if args.extras:
-        line["batched"] = batched_leg(args)
-        line["differentiable"] = differentiable_leg(args)
-        line["narrow_band"] = narrow_band_leg(args)
-        line["convex"] = convex_leg(args)
+        line["batched"] = _leg(batched_leg, args)
+        line["differentiable"] = _leg(differentiable_leg, args)
+        line["narrow_band"] = _leg(narrow_band_leg, args)
+        line["convex"] = _leg(convex_leg, args)
         if not args.no_cpu_baseline:
-            line["cpu_baseline_batched"] = cpu_baseline_batched(args)
+            line["cpu_baseline_batched"] = _leg(cpu_baseline_batched, args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def _leg(fn, args):
+    """One extra leg of the line; a failure is reported in the leg's entry (the headline
+    numbers above it stand on their own)."""
+    try:
+        return fn(args)
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def _timed_median(fn, warmup, steps):
@@ -481,6 +490,16 @@ def narrow_band_leg(args, warmup=1, steps=3):
     return out
 
 
+def convex_sweep_model(f):
+    """(layers d >= 1 with k_d > 0, out-arcs of an interior node, algorithmic bytes per listed
+    node of one push/relabel step) of the convex solve with profile f(1..delta): the node's
+    excess and label, each out-arc word and its far-end label, three atomic words."""
+    f = np.asarray(f, dtype=np.int64)
+    nl = int(np.count_nonzero(np.diff(np.concatenate([[0], f]), 2))) if f.size > 1 else 0
+    arcs = 3 + 4 * (2 + int(f.size > 0 and f[0] > 0) + 2 * nl)
+    return nl, arcs, 20 + 8 * arcs
+
+
 def _energy_pairwise(cost, h, fv):
     """sum_col c(col, h) + sum over 4-neighbour pairs fv[|h_p - h_q|] (numpy, int64)."""
     h = h.astype(np.int64)
@@ -510,9 +529,7 @@ def convex_leg(args, warmup=1, steps=3):
     dt, times, (flow, energy, h, st) = _timed_median(lambda: pog.pog_solve_convex(cost, delta, f, options=opts),
                                                      warmup, steps)
     n = X * Y * Z
-    nl = int(np.count_nonzero(np.diff(np.concatenate([[0], f]), 2)))  # layers d >= 1 with k_d > 0
-    arcs = 3 + 4 * (2 + int(f[0] > 0) + 2 * nl)  # out-arcs of an interior node
-    per_node = 20 + 8 * arcs  # exc, lab, each arc word and head label; three atomic words
+    nl, arcs, per_node = convex_sweep_model(f)
     sweeps = max(int(st["sweeps"]), 1)
     scan = 8 * (n - X * Y)  # k_cv_collect: excess and label of every node above the bottom layer
     sweep_bytes = st["tiles_visited"] * per_node + sweeps * scan

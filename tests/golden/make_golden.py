@@ -5,6 +5,7 @@
     python tests/golden/make_golden.py batch [K]  # the first K volumes of the uneven batch
     python tests/golden/make_golden.py diff [W]   # the 16 float volumes of 128^3, W threads
     python tests/golden/make_golden.py convex     # convex pairwise costs, two mid-size volumes
+    python tests/golden/make_golden.py band       # the benchmark's narrow band (about an hour)
 
 Each file records the workload, the oracle's max-flow value and its surface (in full for
 the small volume; as a SHA-256 of the int32 heights plus their sum otherwise). Nothing
@@ -82,6 +83,30 @@ def record_convex(shape):
             "oracle_seconds": round(time.time() - t, 1)}
 
 
+def record_band():
+    """The narrow band of the 512x512x384 volume around its 64 landmarks (stick 16, band
+    factor 2): band volume and center surface from oracle/band.py, then the band's solve."""
+    from oracle import band as oband
+
+    spec = synth.spec_seismic()
+    cost = synth.horizon_cost(spec)
+    lm = synth.horizon_landmarks(spec, 8)
+    half = synth.BAND_STICK * synth.BAND_FACTOR
+    rb, rc = oband.narrow_band(cost, lm, synth.BAND_STICK, synth.BAND_FACTOR, synth.BAND_OUTSIDE)
+    t = time.time()
+    r = oracle.solve(rb, 3, 50)
+    hb = np.ascontiguousarray(r.heights, dtype=np.int32)
+    himg = np.ascontiguousarray(oband.band_heights(hb, rc, half), dtype=np.int32)
+    sha = lambda a: hashlib.sha256(np.ascontiguousarray(a, dtype=np.int32).tobytes()).hexdigest()  # noqa: E731
+    return {"workload": "narrow band of the 512x512x384 volume (delta 3, alpha 50): 64 landmarks "
+                        "(synth.horizon_landmarks, 8x8), stick 16, band factor 2, outside cost 1200",
+            "oracle": "oracle/band.py construction; explicit-edge Dinic (oracle/pog_oracle.c)",
+            "generator": f"paper_2601_17026_gb300.synth, seed {synth.BASE_SEED}",
+            "band_shape": list(rb.shape), "band_sha256": sha(rb), "center_sha256": sha(rc),
+            "flow": r.flow, "heights_sha256": sha(hb), "heights_sum": int(hb.sum()),
+            "image_heights_sha256": sha(himg), "oracle_seconds": round(time.time() - t, 1)}
+
+
 def main():
     which = sys.argv[1] if len(sys.argv) > 1 else "small"
     if which == "small":
@@ -108,6 +133,8 @@ def main():
                             "hinge target flat at height 64, margin 1024",
                 "oracle": "explicit-edge Dinic (oracle/pog_oracle.c)",
                 "generator": f"paper_2601_17026_gb300.synth, seed {synth.BASE_SEED}", "volumes": vols}
+    elif which == "band":
+        data = record_band()
     elif which == "convex":
         data = {"workload": "layered-horizon volumes (synth.convex_cost), convex pairwise cost f(t) = 4 t^2, "
                             "delta 9 (edge interval of 10)",

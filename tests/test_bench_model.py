@@ -34,3 +34,24 @@ def test_job_throughput_and_roofline_units():
     # 0.456 ms per tiled sweep moving 398.9 MB: 874 GB/s
     by = 398911296.0
     assert abs(by / (0.45645 / 1e3) / 1e9 - 873.9) < 0.1
+
+
+def test_convex_sweep_model():
+    # delta 9, f(t) = 4 t^2: k_0 = 4 and k_1..k_8 = 8, so 8 layers d >= 1 and the pair layer
+    t = [4 * d * d for d in range(1, 10)]
+    nl, arcs, per_node = bench.convex_sweep_model(t)
+    assert nl == 8
+    assert arcs == 3 + 4 * (2 + 1 + 16) == 79   # sink, down, up; per direction hard out/in, pair, 8 x 2 layer arcs
+    assert per_node == 20 + 8 * 79 == 652
+    # the linear profile has the pair layer only; the hinge profile 7 (t - 1)^+ one layer d = 1
+    assert bench.convex_sweep_model([3, 6, 9]) == (0, 3 + 4 * 3, 20 + 8 * 15)
+    assert bench.convex_sweep_model([0, 7, 14])[:2] == (1, 3 + 4 * (2 + 0 + 2))
+    assert bench.convex_sweep_model([]) == (0, 3 + 4 * 2, 20 + 8 * 11)
+
+
+def test_convex_traffic_is_gated_by_the_kernel_source():
+    entry = bench.MEASURED_TRAFFIC["k_cv_push_relabel"]
+    if entry["source_sha"] == bench._source_sha("k_cv_push_relabel"):
+        assert bench.measured_traffic("k_cv_push_relabel", 1000) == entry["bytes_per_unit"] * 1000
+    else:
+        assert bench.measured_traffic("k_cv_push_relabel", 1000) is None
