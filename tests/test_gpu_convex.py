@@ -153,6 +153,18 @@ def test_full_size_energy_identity_and_local_optimality():
     assert pins.energy_pairwise(cost, h, fv) == e
 
 
+def test_full_size_schedule_independence():
+    """The minimal cut is unique: two very different sweep schedules on the benchmark volume
+    give the same flow and the same surface, bit for bit."""
+    X, Y, Z = synth.CONVEX_SHAPE
+    cost = synth.convex_cost(X, Y, Z)
+    f = synth.convex_profile()
+    a = gpu_convex(cost, synth.CONVEX_DELTA, f, sweeps_per_relabel=16)
+    b = gpu_convex(cost, synth.CONVEX_DELTA, f, sweeps_per_relabel=200, flags=pog.POG_FLAG_NO_PREPUSH)
+    assert a[0] == b[0] and a[1] == b[1]
+    np.testing.assert_array_equal(a[2], b[2])
+
+
 def test_invalid_arguments_and_failures():
     cost = torch.zeros((3, 3, 5), dtype=torch.int32, device="cuda")
     with pytest.raises(pog.PogError) as ei:
