@@ -35,6 +35,39 @@ def test_band_construction_full_size():
     assert torch.equal(b.cpu(), torch.from_numpy(rb))
 
 
+def test_band_solve_full_size_matches_stored_oracle():
+    """The benchmark's band (17M nodes, delta 3, alpha 50) solved in the bench's launch
+    configuration: flow, band surface and image heights against the oracle's stored Dinic
+    result (tests/golden/band.json)."""
+    import hashlib
+    import json
+    import os
+
+    from paper_2601_17026_gb300 import autotune
+
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "band.json")
+    if not os.path.exists(gold):
+        pytest.skip("no stored oracle result for the full-size band")
+    with open(gold) as fh:
+        ref = json.load(fh)
+    spec = synth.spec_seismic()
+    cost = synth.horizon_cost(spec)
+    lm = synth.horizon_landmarks(spec, 8)
+    half = synth.BAND_STICK * synth.BAND_FACTOR
+    b, c = _gpu_band(cost, lm, synth.BAND_STICK, synth.BAND_FACTOR, synth.BAND_OUTSIDE)
+    X, Y, Zb = b.shape
+    opts = pog.make_options(**autotune.tuned_params(X, Y, Zb, 3, 50))
+    with pog.pog_build(b, 3, 50, opts) as g:
+        flow = pog.pog_maxflow(g)
+        hb = pog.pog_surface(g)
+        himg = pog.pog_band_heights(hb, c, half)
+    sha = lambda t: hashlib.sha256(t.cpu().numpy().astype(np.int32).tobytes()).hexdigest()  # noqa: E731
+    assert sha(b) == ref["band_sha256"] and sha(c) == ref["center_sha256"]
+    assert flow == ref["flow"]
+    assert sha(hb) == ref["heights_sha256"] and int(hb.sum().item()) == ref["heights_sum"]
+    assert sha(himg) == ref["image_heights_sha256"]
+
+
 @pytest.mark.parametrize("grid,stick,factor", [(4, 6, 2), (3, 5, 1), (1, 20, 3)])
 def test_band_solve_matches_oracle(grid, stick, factor):
     spec = synth.scaled_spec(48, 40, 96, 29, stream=30)
