@@ -14,6 +14,12 @@ Pins (see ``tests/test_oracle_pins.py``): brute-force enumeration of all feasibl
 surfaces on tiny volumes, the closed form for delta >= Z-1 without soft penalty,
 an exact dynamic program over one row of columns, the energy/flow identity, and the
 capacity / conservation / max-flow = min-cut invariants checked inside the C code.
+
+``solve_convex`` builds the same literal graph with a convex pairwise cost f over the
+edge interval (one layer of soft arcs per height drop, capacity the second difference of
+f) and runs the same Dinic; ``energy_convex`` is that energy from its definition. Pins in
+``tests/test_convex_pins.py``: enumeration, the single-row dynamic program with f, the
+energy identity, the linear profile against ``solve``, and planted mistakes.
 """
 from __future__ import annotations
 
