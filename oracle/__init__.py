@@ -66,6 +66,15 @@ def _configure(lib):
     lib.oracle_energy_convex.restype = ctypes.c_int64
     lib.oracle_energy_convex.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, i64p, i32p, i32p]
+    lib.oracle_cut_capacity_convex.restype = ctypes.c_int64
+    lib.oracle_cut_capacity_convex.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, i64p, i32p]
+    lib.oracle_solve_state_convex.restype = ctypes.c_int
+    lib.oracle_solve_state_convex.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              i64p, i64p, i32p, i32p, i32p, i32p, i32p, i32p, i32p, i32p]
+    lib.oracle_certify_convex.restype = ctypes.c_int
+    lib.oracle_certify_convex.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          i64p, i32p, i32p, i32p, i32p, i32p, i32p, i32p, i32p, ctypes.c_int64]
     lib.oracle_energy.restype = ctypes.c_int64
     lib.oracle_energy.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_int64, i32p, i32p]
@@ -171,6 +180,66 @@ def energy_convex(cost, heights, delta: int, f):
     e = lib.oracle_energy_convex(_i32(c), X, Y, Z, int(delta), fa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                  _i32(h), ctypes.byref(feas))
     return int(e), bool(feas.value)
+
+
+CONVEX_STATE_KEYS = ("excess", "sink", "fdown", "fhard", "gpair", "flayer", "in_cut")
+
+
+def _i64(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def cut_capacity_convex(cost, heights, delta: int, f) -> int:
+    """Eq. 6 for the cut below the surface, arc by arc over the literal layered graph; -1 when
+    an infinite arc crosses it."""
+    lib = _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    fa = _profile(delta, f)
+    h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
+    return int(lib.oracle_cut_capacity_convex(_i32(c), X, Y, Z, int(delta), _i64(fa), _i32(h)))
+
+
+def solve_state_convex(cost, delta: int, f, lib=None):
+    """(flow, heights, state): the oracle's max flow of the convex-cost graph in a solver-state
+    layout (the dict ``certify_convex`` takes; flayer holds (delta - 1) * 4 arrays of N words,
+    layer d = 1.. and direction 0..3)."""
+    lib = lib or _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    N = X * Y * Z
+    fa = _profile(delta, f)
+    heights = np.empty((X, Y), dtype=np.int32)
+    st = {k: np.empty(N, dtype=np.int32) for k in ("excess", "sink", "fdown", "in_cut")}
+    st["fhard"] = np.empty(4 * N, dtype=np.int32)
+    st["gpair"] = np.empty(2 * N, dtype=np.int32)
+    st["flayer"] = np.zeros(max(4 * (delta - 1), 1) * N, dtype=np.int32)
+    flow = ctypes.c_int64(0)
+    rc = lib.oracle_solve_state_convex(_i32(c), X, Y, Z, int(delta), _i64(fa), ctypes.byref(flow), _i32(heights),
+                                       _i32(st["excess"]), _i32(st["sink"]), _i32(st["fdown"]), _i32(st["fhard"]),
+                                       _i32(st["gpair"]), _i32(st["flayer"]), _i32(st["in_cut"]))
+    if rc != 0:
+        raise RuntimeError(f"oracle_solve_state_convex failed: {ERRORS.get(rc, rc)}")
+    return int(flow.value), heights, st
+
+
+def certify_convex(cost, delta: int, f, state: dict, flow: int, heights, lib=None) -> int:
+    """O(N) certificate of a convex-cost state (see ``solve_state_convex``); 0 means the
+    preflow is feasible with value `flow`, the cut below `heights` has capacity `flow`, and the
+    cut is the residual reach of the excess nodes. See CERTIFY_ERRORS."""
+    lib = lib or _load()
+    c = _cost(cost)
+    X, Y, Z = c.shape
+    N = X * Y * Z
+    fa = _profile(delta, f)
+    arr = {k: np.ascontiguousarray(state[k], dtype=np.int32) for k in CONVEX_STATE_KEYS}
+    if arr["flayer"].size < max(4 * (delta - 1), 1) * N:
+        raise ValueError("flayer must hold 4 * (delta - 1) arrays of N words")
+    h = np.ascontiguousarray(heights, dtype=np.int32).reshape(X, Y)
+    return int(lib.oracle_certify_convex(_i32(c), X, Y, Z, int(delta), _i64(fa), _i32(arr["excess"]),
+                                         _i32(arr["sink"]), _i32(arr["fdown"]), _i32(arr["fhard"]),
+                                         _i32(arr["gpair"]), _i32(arr["flayer"]), _i32(arr["in_cut"]), _i32(h),
+                                         int(flow)))
 
 
 def solve_state(cost, delta: int, alpha: int, lib=None):

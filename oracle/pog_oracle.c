@@ -702,3 +702,305 @@ out:
     free(queue);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Convex pairwise costs: the oracle's own final flow in a solver-state layout, the literal
+ * cut capacity of a surface, and the O(N) certificate of a state.
+ *
+ * State layout (int32 arrays, z fastest, N = X*Y*Z, the bottom layer merged into the source as
+ * in oracle_solve_state): excess, sink, fdown, fhard[4N] as there; gpair[2N] = net flow of the
+ * d = 0 layer from v to its neighbour at x+1 (k = 0) or y+1 (k = 1), in [-k_0, k_0];
+ * flayer[((d-1)*4 + dir)*N + v] = flow on the layer-d arc from v to its neighbour in direction
+ * dir at height z - d (present when z - d >= 1 and k_d > 0), d = 1 .. delta-1; in_cut.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Capacity (Eq. 6) of the cut whose source side is {s} and, in each column, the nodes
+ * z <= h(col), counted arc by arc over the literal layered graph; -1 when an infinite arc
+ * crosses it. f as for oracle_solve_convex. */
+int64_t oracle_cut_capacity_convex(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta,
+                                   const int64_t *f, const int32_t *h) {
+    int64_t *kcap = malloc(((size_t)delta + 1) * sizeof(int64_t));
+    if (!kcap) return -2;
+    if (!convex_layers(f, delta, kcap)) {
+        free(kcap);
+        return -2;
+    }
+    const int64_t bsum = bottom_layer_sum(cost, X, Y, Z);
+    int64_t cut = 0;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t z = 0; z < Z; ++z) {
+                const int in_u = z <= h[x * Y + y];
+                const int64_t w = node_weight(cost, X, Y, Z, x, y, z, bsum);
+                if (w < 0 && !in_u) cut += -w;
+                if (w > 0 && in_u) cut += w;
+                if (!in_u) continue;
+                if (z >= 1 && !(z - 1 <= h[x * Y + y])) { cut = -1; goto done; }
+                for (int d = 0; d < 4; ++d) {
+                    const int64_t xq = x + DX[d], yq = y + DY[d];
+                    if (xq < 0 || xq >= X || yq < 0 || yq >= Y) continue;
+                    const int64_t hq = h[xq * Y + yq];
+                    const int64_t zq = (z - delta > 0) ? z - delta : 0;
+                    if (!(zq <= hq)) { cut = -1; goto done; }
+                    for (int64_t l = 0; l < delta; ++l)
+                        if (kcap[l] > 0 && z - l >= 0 && !(z - l <= hq)) cut += kcap[l];
+                }
+            }
+done:
+    free(kcap);
+    return cut;
+}
+
+int oracle_solve_state_convex(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta, const int64_t *f,
+                              int64_t *flow_out, int32_t *heights_out, int32_t *excess, int32_t *sink,
+                              int32_t *fdown, int32_t *fhard, int32_t *gpair, int32_t *flayer, int32_t *in_cut) {
+    if (!cost || X < 1 || Y < 1 || Z < 1 || delta < 0 || (delta > 0 && !f) || !flow_out || !heights_out ||
+        !excess || !sink || !fdown || !fhard || !gpair || (delta > 1 && !flayer) || !in_cut)
+        return ORC_E_ARGS;
+    if ((int64_t)X * Y * Z + 2 > INT32_MAX) return ORC_E_ARGS;
+    int64_t *kcap = malloc(((size_t)delta + 1) * sizeof(int64_t));
+    if (!kcap) return ORC_E_NOMEM;
+    if (!convex_layers(f, delta, kcap)) {
+        free(kcap);
+        return ORC_E_ARGS;
+    }
+    orc_graph g;
+    int rc = graph_build(&g, cost, X, Y, Z, delta, kcap, delta, 1);
+    if (rc != ORC_OK) {
+        free(kcap);
+        return rc;
+    }
+    const int64_t N = (int64_t)X * Y * Z, s = N, t = N + 1;
+    const int64_t nl = delta > 1 ? delta - 1 : 0;
+    orc_dinic d = {0};
+    d.level = malloc((size_t)g.n * sizeof(int32_t));
+    d.queue = malloc((size_t)g.n * sizeof(int64_t));
+    d.iter = malloc((size_t)g.n * sizeof(int64_t));
+    d.path = malloc((size_t)g.n * sizeof(int64_t));
+    uint8_t *in_s = malloc((size_t)g.n);
+    int64_t *acc = calloc((size_t)N * (9 + 4 * nl), sizeof(int64_t)); /* excess fdown fhard[4] gpair[2] sink flayer */
+    if (!d.level || !d.queue || !d.iter || !d.path || !in_s || !acc) {
+        rc = ORC_E_NOMEM;
+        goto done;
+    }
+    int64_t flow = 0;
+    while (dinic_bfs(&g, &d, s, t)) flow += dinic_blocking_flow(&g, &d, s, t);
+    residual_reach(&g, s, in_s, d.queue);
+    int64_t *exc = acc, *fdn = acc + N, *fh = acc + 2 * N, *gp = acc + 6 * N, *snk = acc + 8 * N, *fl = acc + 9 * N;
+    for (int64_t a = g.first[s]; a < g.first[s + 1]; ++a) {
+        const int64_t v = g.head[a];
+        if (g.cap0[a] > 0 && v % Z != 0) exc[v] += g.cap[a];
+    }
+    for (int64_t u = 0; u < N; ++u) {
+        const int64_t z = u % Z, col = u / Z, x = col / Y, y = col % Y;
+        if (z == 0) continue;
+        for (int64_t a = g.first[u]; a < g.first[u + 1]; ++a) {
+            if (g.cap0[a] <= 0) continue; /* a reverse half-arc */
+            const int64_t h = g.head[a], fa = g.cap0[a] - g.cap[a];
+            if (h == t) {
+                snk[u] = g.cap[a];
+                continue;
+            }
+            const int64_t hz = h % Z, hcol = h / Z, hx = hcol / Y, hy = hcol % Y;
+            if (hz == 0) { /* into the bottom layer: not an arc of the state */
+                exc[u] += fa;
+                continue;
+            }
+            if (hcol == col) {
+                fdn[u] += fa;
+                continue;
+            }
+            int dir = -1;
+            for (int k = 0; k < 4; ++k)
+                if (hx == x + DX[k] && hy == y + DY[k]) dir = k;
+            if (dir < 0) {
+                rc = ORC_E_ARGS;
+                goto done;
+            }
+            const int64_t drop = z - hz;
+            if (g.cap0[a] == ORC_INF) {
+                fh[dir * N + u] += fa;
+            } else if (drop == 0) {
+                if (dir & 1) gp[(dir >> 1) * N + u] += fa;
+                else gp[(dir >> 1) * N + h] -= fa;
+            } else if (drop >= 1 && drop < delta) {
+                fl[((drop - 1) * 4 + dir) * N + u] += fa;
+            } else {
+                rc = ORC_E_ARGS;
+                goto done;
+            }
+        }
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        const int bottom = v % Z == 0;
+        excess[v] = bottom ? 0 : (int32_t)exc[v];
+        sink[v] = bottom ? 0 : (int32_t)snk[v];
+        fdown[v] = bottom ? 0 : (int32_t)fdn[v];
+        for (int k = 0; k < 4; ++k) fhard[k * N + v] = bottom ? 0 : (int32_t)fh[k * N + v];
+        for (int k = 0; k < 2; ++k) gpair[k * N + v] = bottom ? 0 : (int32_t)gp[k * N + v];
+        for (int64_t j = 0; j < 4 * nl; ++j) flayer[j * N + v] = bottom ? 0 : (int32_t)fl[j * N + v];
+        in_cut[v] = in_s[v];
+    }
+    for (int64_t col = 0; col < (int64_t)X * Y; ++col) {
+        int32_t hgt = -1;
+        for (int64_t z = 0; z < Z; ++z)
+            if (in_s[col * Z + z]) hgt = (int32_t)z;
+        heights_out[col] = hgt;
+        if (hgt < 0) rc = ORC_E_SURFACE;
+    }
+    *flow_out = flow;
+done:
+    free(d.level);
+    free(d.queue);
+    free(d.iter);
+    free(d.path);
+    free(in_s);
+    free(acc);
+    free(kcap);
+    graph_free(&g);
+    return rc;
+}
+
+/*
+ * Optimality certificate of a convex-cost state (layout above), the checks and return codes
+ * of oracle_certify: capacity of every arc and sink arc with zero flow on absent arcs (10),
+ * excess = inflow - outflow >= 0 (11), the preflow's value equals `flow` (12), the cut marks
+ * equal the residual reach of the nodes with excess (13), each height is the top marked node
+ * of its column (14), and the literal capacity of the cut below the heights equals `flow`
+ * (15). ORC_E_ARGS when f is not convex.
+ */
+int oracle_certify_convex(const int32_t *cost, int32_t X, int32_t Y, int32_t Z, int32_t delta, const int64_t *f,
+                          const int32_t *excess, const int32_t *sink, const int32_t *fdown, const int32_t *fhard,
+                          const int32_t *gpair, const int32_t *flayer, const int32_t *in_cut, const int32_t *heights,
+                          int64_t flow) {
+    const int64_t N = (int64_t)X * Y * Z;
+    const int64_t nl = delta > 1 ? delta - 1 : 0;
+    const int64_t bsum = bottom_layer_sum(cost, X, Y, Z);
+    int64_t *kcap = malloc(((size_t)delta + 1) * sizeof(int64_t));
+    int64_t *net = calloc((size_t)N, sizeof(int64_t));
+    uint8_t *seen = calloc((size_t)N, 1);
+    int64_t *queue = malloc((size_t)N * sizeof(int64_t));
+    int rc = ORC_OK;
+    if (!kcap || !net || !seen || !queue) {
+        rc = ORC_E_NOMEM;
+        goto out;
+    }
+    if (!convex_layers(f, delta, kcap)) {
+        rc = ORC_E_ARGS;
+        goto out;
+    }
+    const int64_t k0 = delta > 0 ? kcap[0] : 0;
+    int64_t value = 0;
+    for (int64_t x = 0; x < X; ++x)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t z = 0; z < Z; ++z) {
+                const int64_t v = idx3(Y, Z, x, y, z);
+                const int64_t w = node_weight(cost, X, Y, Z, x, y, z, bsum);
+                if (z == 0) { /* part of the source: no state of its own */
+                    if (w > 0) value += w;
+                    if (sink[v] != 0 || fdown[v] != 0 || excess[v] != 0) { rc = 10; goto out; }
+                    for (int d = 0; d < 4; ++d)
+                        if (fhard[d * N + v] != 0 || (d < 2 && gpair[d * N + v] != 0)) { rc = 10; goto out; }
+                    for (int64_t j = 0; j < 4 * nl; ++j)
+                        if (flayer[j * N + v] != 0) { rc = 10; goto out; }
+                    continue;
+                }
+                const int64_t snk0 = w > 0 ? w : 0;
+                if (sink[v] < 0 || sink[v] > snk0) { rc = 10; goto out; }
+                net[v] += (w < 0 ? -w : 0) - (snk0 - sink[v]);
+                value += snk0 - sink[v];
+                if (z >= 2) {
+                    if (fdown[v] < 0) { rc = 10; goto out; }
+                    net[v] -= fdown[v];
+                    net[v - 1] += fdown[v];
+                } else if (fdown[v] != 0) { rc = 10; goto out; }
+                for (int d = 0; d < 4; ++d) {
+                    const int64_t xq = x + DX[d], yq = y + DY[d];
+                    const int in_grid = xq >= 0 && xq < X && yq >= 0 && yq < Y;
+                    const int64_t fhv = fhard[d * N + v];
+                    if (in_grid && z - delta >= 1) {
+                        if (fhv < 0) { rc = 10; goto out; }
+                        const int64_t head = idx3(Y, Z, xq, yq, z - delta);
+                        net[v] -= fhv;
+                        net[head] += fhv;
+                    } else if (fhv != 0) { rc = 10; goto out; }
+                    if (d & 1) { /* the d = 0 pair towards x+1 / y+1 */
+                        const int64_t gv = gpair[(d >> 1) * N + v];
+                        if (in_grid && k0 > 0) {
+                            if (gv < -k0 || gv > k0) { rc = 10; goto out; }
+                            net[v] -= gv;
+                            net[idx3(Y, Z, xq, yq, z)] += gv;
+                        } else if (gv != 0) { rc = 10; goto out; }
+                    }
+                    for (int64_t dd = 1; dd < delta; ++dd) {
+                        const int64_t fl = flayer[((dd - 1) * 4 + d) * N + v];
+                        if (in_grid && z - dd >= 1 && kcap[dd] > 0) {
+                            if (fl < 0 || fl > kcap[dd]) { rc = 10; goto out; }
+                            net[v] -= fl;
+                            net[idx3(Y, Z, xq, yq, z - dd)] += fl;
+                        } else if (fl != 0) { rc = 10; goto out; }
+                    }
+                }
+            }
+    for (int64_t v = 0; v < N; ++v) {
+        if (v % Z == 0) continue;
+        if (net[v] != excess[v] || excess[v] < 0) { rc = 11; goto out; }
+    }
+    if (value != flow) { rc = 12; goto out; }
+    /* residual reach of the excess nodes (z >= 1 only; the bottom layer is the source) */
+    int64_t qh = 0, qt = 0;
+    for (int64_t v = 0; v < N; ++v)
+        if (v % Z != 0 && excess[v] > 0) { seen[v] = 1; queue[qt++] = v; }
+    while (qh < qt) {
+        const int64_t u = queue[qh++];
+        const int64_t z = u % Z, col = u / Z, x = col / Y, y = col % Y;
+#define ORC_REACH(node)                                  \
+    do {                                                 \
+        const int64_t _n = (node);                       \
+        if (!seen[_n]) { seen[_n] = 1; queue[qt++] = _n; } \
+    } while (0)
+        if (z >= 2) ORC_REACH(u - 1);                        /* down arc: infinite */
+        if (z + 1 < Z && fdown[u + 1] > 0) ORC_REACH(u + 1); /* reverse of the down arc above */
+        for (int d = 0; d < 4; ++d) {
+            const int64_t xq = x + DX[d], yq = y + DY[d];
+            if (xq < 0 || xq >= X || yq < 0 || yq >= Y) continue;
+            if (z - delta >= 1) ORC_REACH(idx3(Y, Z, xq, yq, z - delta));
+            if (z + delta < Z) {
+                const int64_t wq = idx3(Y, Z, xq, yq, z + delta);
+                if (fhard[(d ^ 1) * N + wq] > 0) ORC_REACH(wq);
+            }
+            if (k0 > 0) {
+                const int64_t q = idx3(Y, Z, xq, yq, z);
+                const int64_t gv = (d & 1) ? gpair[(d >> 1) * N + u] : -gpair[(d >> 1) * N + q];
+                if (k0 - gv > 0) ORC_REACH(q); /* gv: net flow u -> q */
+            }
+            for (int64_t dd = 1; dd < delta; ++dd) {
+                if (kcap[dd] <= 0) continue;
+                if (z - dd >= 1 && kcap[dd] - flayer[((dd - 1) * 4 + d) * N + u] > 0)
+                    ORC_REACH(idx3(Y, Z, xq, yq, z - dd));
+                if (z + dd < Z) { /* reverse of the layer arc of (q, z+dd) into u */
+                    const int64_t wq = idx3(Y, Z, xq, yq, z + dd);
+                    if (flayer[((dd - 1) * 4 + (d ^ 1)) * N + wq] > 0) ORC_REACH(wq);
+                }
+            }
+        }
+#undef ORC_REACH
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        if (v % Z == 0) continue;
+        if ((in_cut[v] != 0) != (seen[v] != 0)) { rc = 13; goto out; }
+    }
+    for (int64_t col = 0; col < (int64_t)X * Y; ++col) {
+        int32_t top = 0;
+        for (int64_t z = 1; z < Z; ++z)
+            if (in_cut[col * Z + z]) top = (int32_t)z;
+        if (heights[col] != top) { rc = 14; goto out; }
+    }
+    if (oracle_cut_capacity_convex(cost, X, Y, Z, delta, f, heights) != flow) rc = 15;
+out:
+    free(kcap);
+    free(net);
+    free(seen);
+    free(queue);
+    return rc;
+}

@@ -6,7 +6,10 @@ oracle builds it literally, one layer of soft arcs per height drop d < delta wit
 second difference of f as capacity, and runs Dinic. Pins: enumeration of every surface
 on tiny volumes, the single-row dynamic program with f in place of alpha |.|, the
 flow/energy identity with the energy computed from its definition, the linear profile
-against the alpha solve, and planted mistakes in the layer construction.
+against the alpha solve, and planted mistakes in the layer construction. The O(N)
+certificate of a convex-cost state (for volumes too large for Dinic) is pinned by accepting
+the oracle's own optimal state and rejecting one-word changes of it, one per check, and a
+feasible preflow below the maximum.
 """
 import os
 import shutil
@@ -175,3 +178,129 @@ def test_planted_convex_mistakes(name, tmp_path):
 def test_unmutated_passes_convex_mutant_pins():
     lib = oracle._load()
     assert _convex_pins_pass(lib)
+
+
+# --------------------------------------------------------------------------------------
+# The literal cut capacity and the O(N) certificate of a convex-cost state.
+# --------------------------------------------------------------------------------------
+
+def _kcap(delta, f):
+    fv = _fv(f)
+    return [int(fv[1])] + [int(fv[d + 1] - 2 * fv[d] + fv[d - 1]) for d in range(1, delta)] if delta else []
+
+
+def test_cut_capacity_convex_is_energy_plus_offset():
+    """Every feasible surface: literal arc count = E(h) + K; infeasible: -1."""
+    rng = np.random.default_rng(41)
+    for _ in range(60):
+        delta = int(rng.integers(0, 5))
+        f = list(pins.convex_profiles(delta).values())[int(rng.integers(0, 5))]
+        X, Y, Z = int(rng.integers(1, 5)), int(rng.integers(1, 5)), int(rng.integers(2, 8))
+        cost = _rand_cost(rng, X, Y, Z)
+        h = rng.integers(0, Z, size=(X, Y))
+        e, ok = oracle.energy_convex(cost, h, delta, f)
+        cut = oracle.cut_capacity_convex(cost, h, delta, f)
+        if ok:
+            assert cut == e + pins.identity_offset(cost)
+            assert e == pins.energy_pairwise(cost, h, _fv(f))
+        else:
+            assert cut == -1
+
+
+CERT_CASES = [((2, 3, 5), 2), ((3, 2, 6), 3), ((4, 4, 7), 4), ((1, 5, 8), 1), ((5, 1, 6), 0), ((3, 3, 4), 7),
+              ((4, 3, 9), 9)]
+
+
+@pytest.mark.parametrize("shape,delta", CERT_CASES)
+def test_certificate_convex_accepts_the_oracles_optimal_state(shape, delta):
+    rng = np.random.default_rng(hash((shape, delta, "cert")) % (2**32))
+    for name, f in pins.convex_profiles(delta).items():
+        for lo, hi in ((-30, 50), (-400, 400)):
+            cost = _rand_cost(rng, *shape, lo=lo, hi=hi)
+            flow, h, st = oracle.solve_state_convex(cost, delta, f)
+            ref = oracle.solve_convex(cost, delta, f)
+            assert flow == ref.flow and np.array_equal(h, ref.heights)
+            assert oracle.certify_convex(cost, delta, f, st, flow, h) == 0, name
+
+
+def _zero_state_convex(cost, delta, f):
+    """The convex graph's preflow before any push, its value, its residual reach and the
+    heights of that cut (python BFS over the merged graph, tiny volumes only)."""
+    X, Y, Z = cost.shape
+    N = X * Y * Z
+    w = pins.node_weights(cost).reshape(-1)
+    upper = (np.arange(N) % Z) != 0
+    k = _kcap(delta, f)
+    st = {"excess": np.where(upper & (w < 0), -w, 0).astype(np.int32),
+          "sink": np.where(upper & (w > 0), w, 0).astype(np.int32),
+          "fdown": np.zeros(N, np.int32), "fhard": np.zeros(4 * N, np.int32), "gpair": np.zeros(2 * N, np.int32),
+          "flayer": np.zeros(max(4 * (delta - 1), 1) * N, np.int32)}
+    idx = lambda x, y, z: (x * Y + y) * Z + z  # noqa: E731
+    seen = set(int(v) for v in np.flatnonzero(st["excess"] > 0))
+    todo = list(seen)
+    while todo:
+        u = todo.pop()
+        z, col = u % Z, u // Z
+        x, y = col // Y, col % Y
+        nxt = [u - 1] if z >= 2 else []
+        for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+            xq, yq = x + dx, y + dy
+            if not (0 <= xq < X and 0 <= yq < Y):
+                continue
+            if z - delta >= 1:
+                nxt.append(idx(xq, yq, z - delta))
+            for d in range(delta):
+                if k[d] > 0 and z - d >= 1:
+                    nxt.append(idx(xq, yq, z - d))
+        for v in nxt:
+            if v not in seen:
+                seen.add(v)
+                todo.append(v)
+    st["in_cut"] = np.zeros(N, np.int32)
+    st["in_cut"][list(seen)] = 1
+    heights = np.where(st["in_cut"].reshape(X, Y, Z) > 0, np.arange(Z), 0).max(axis=2)
+    b = pins.node_weights(cost)[:, :, 0]
+    return st, int(b[b > 0].sum()), heights
+
+
+def test_certificate_convex_rejects_one_word_changes():
+    """One change per check (10-15) of an optimal state, and a feasible but non-maximum
+    preflow (the state before any push) for the last check."""
+    rng = np.random.default_rng(52)
+    shape, delta = (3, 4, 7), 3
+    f = pins.convex_profiles(delta)["quadratic"]
+    X, Y, Z = shape
+    N = X * Y * Z
+    for _ in range(5):
+        cost = _rand_cost(rng, *shape)
+        flow, h, st = oracle.solve_state_convex(cost, delta, f)
+        assert oracle.certify_convex(cost, delta, f, st, flow, h) == 0
+
+        def with_change(key, i, val):
+            s2 = {k: v.copy() for k, v in st.items()}
+            s2[key][i] = val
+            return s2
+
+        v = (1 * Y + 2) * Z + 4                    # an interior node with every layer arc present
+        d1 = ((1 - 1) * 4 + 1) * N + v             # its layer-1 arc towards x+1
+        assert oracle.certify_convex(cost, delta, f, with_change("flayer", d1, 8 + 1), flow, h) == 10
+        assert oracle.certify_convex(cost, delta, f, with_change("flayer", 0 * N + 0, 1), flow, h) == 10  # bottom
+        assert oracle.certify_convex(cost, delta, f, with_change("gpair", v, 2 + 1), flow, h) == 10
+        assert oracle.certify_convex(cost, delta, f, with_change("excess", v, st["excess"][v] + 1), flow, h) == 11
+        assert oracle.certify_convex(cost, delta, f, st, flow + 1, h) == 12
+        u = int(np.flatnonzero((np.arange(N) % Z != 0))[3])
+        assert oracle.certify_convex(cost, delta, f, with_change("in_cut", u, 1 - st["in_cut"][u]), flow, h) == 13
+        h2 = h.copy()
+        h2[0, 0] = (h2[0, 0] + 1) % Z
+        assert oracle.certify_convex(cost, delta, f, st, flow, h2) == 14
+    # the state before any push is a feasible preflow; the certificate rejects it (check 15)
+    # whenever its value is below the maximum
+    rejected = 0
+    for _ in range(6):
+        cost = _rand_cost(rng, *shape)
+        st0, value0, h0 = _zero_state_convex(cost, delta, f)
+        best = oracle.solve_convex(cost, delta, f).flow
+        code = oracle.certify_convex(cost, delta, f, st0, value0, h0)
+        assert code == (0 if value0 == best else 15)
+        rejected += code == 15
+    assert rejected > 0
